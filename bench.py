@@ -1,0 +1,430 @@
+#!/usr/bin/env python3
+"""Benchmark of the finite-element Kohn-Sham slab hot path on GB300.
+
+One step = one pass of the whole hot path on the p = 5 constant-field slab (16 x 16 x 48
+cells, 1,529,600 psi nodes, 256 pseudo-atoms, field 0.005 Ha/bohr, 512 vectors):
+  Poisson load + Jacobi-CG solve with the CEF boundary conditions and V_eff assembly,
+  the degree-30 Chebyshev filter, Cholesky-QR and Rayleigh-Ritz (one more H X).
+Metric: nominal cell-matrix flops (2 n_e^2 per cell per vector per H X) of all H X
+applications in the step divided by the step's device time, in TFLOP/s.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+For N > 1 run under torch.distributed.run: every rank runs an independent replica on its
+own GPU (the path has no data exchange between slabs), the step time is the maximum over
+ranks and the value the work of all ranks over that time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+R_FILTER = 0.03          # filter cut a = a0 + 0.03 (b - a0)
+POISSON_RTOL = 1e-10
+LANCZOS_STEPS = 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--prec", choices=["f32", "f64", "bf16", "f32x3"], default="f32")
+    ap.add_argument("--workload", choices=["p5", "p5s", "p3"], default="p5")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    """p5: the benchmark slab; p5s: the same p = 5 cells and vectors with 16 cell layers and
+    256 vectors (a 0.5 GB block, above L2) for profiler captures; p3: the small CEF slab."""
+    if name == "p5":
+        return W.config2()
+    if name == "p5s":
+        s = W.config2()
+        return W.Slab(s.name.replace("96", "32") + "-short", (s.L[0], s.L[1], 32.0),
+                      (16, 16, 16), 5, s.R - np.array([0.0, 0.0, 32.0]), s.Z, s.bias, nvec=256,
+                      degree=s.degree, seed=s.seed)
+    return W.config1()
+
+
+def nominal_flops_per_hx(slab, nvec):
+    ne = (slab.p + 1) ** 3
+    return 2.0 * ne * ne * slab.n_cells * nvec
+
+
+def workload_desc(slab):
+    nx, ny, nz = slab.ncell
+    return (f"{slab.name}: {nx}x{ny}x{nz} cells, p={slab.p}, {slab.n_psi:,} psi nodes, "
+            f"{slab.nvec} vectors, Chebyshev degree {slab.degree}, {len(slab.R)} atoms, "
+            f"{slab.bias.kind.upper()} field {slab.bias.field}")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel_key]
+    except Exception:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if h != rec.get("source_sha"):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(dev):
+    import torch
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v for v in vis.split(",") if v.strip()]
+        if dev.index < len(ids) and ids[dev.index].strip().isdigit():
+            return int(ids[dev.index])
+    return dev.index if dev.index is not None else torch.cuda.current_device()
+
+
+def cpu_baseline_oracle(slab, nvec, seed=5):
+    """Oracle CSR H X on a 2-cell-thick slice of the same slab (bounded CPU sample)."""
+    from oracle import assembly
+    from oracle.mesh import Mesh as OMesh
+    nc = (slab.ncell[0], slab.ncell[1], 2)
+    L = (slab.L[0], slab.L[1], 2 * slab.L[2] / slab.ncell[2])
+    om = OMesh(L, nc, slab.p, slab.psi_dirichlet)
+    rng = np.random.default_rng(seed)
+    H = assembly.hamiltonian(om, rng.uniform(-1, 0.5, om.n_psi))
+    X = rng.standard_normal((om.n_psi, nvec))
+    H @ X[:, :8]
+    t0 = time.perf_counter()
+    H @ X
+    dt = time.perf_counter() - t0
+    ne = (slab.p + 1) ** 3
+    flops = 2.0 * ne * ne * om.n_cells * nvec
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle scipy CSR Ht X, one application, {nc[0]}x{nc[1]}x{nc[2]} cells "
+                       f"slice of the slab (p={slab.p}, {om.n_psi:,} psi nodes x {nvec} "
+                       f"vectors), single-threaded sparse kernel, {dt:.2f} s"),
+            "seconds": dt}
+
+
+# ------------------------------------------------------------------------------------------
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    slab = workload(args.workload)
+    from oracle import assembly
+    from oracle.mesh import Mesh as OMesh
+    nc = (slab.ncell[0], slab.ncell[1], 2)
+    L = (slab.L[0], slab.L[1], 2 * slab.L[2] / slab.ncell[2])
+    om = OMesh(L, nc, slab.p, slab.psi_dirichlet)
+    rng = np.random.default_rng(5)
+    H = assembly.hamiltonian(om, rng.uniform(-1, 0.5, om.n_psi))
+    nvec = slab.nvec
+    X = rng.standard_normal((om.n_psi, nvec))
+    ne = (slab.p + 1) ** 3
+    flops = 2.0 * ne * ne * om.n_cells * nvec
+    for _ in range(args.warmup):
+        H @ X
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        H @ X
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    val = flops / dt / 1e12
+    sample = (f"one oracle scipy CSR Ht X per step on a {nc[0]}x{nc[1]}x{nc[2]}-cell slice of "
+              f"the slab (p={slab.p}, {om.n_psi:,} psi nodes x {nvec} vectors)")
+    line = {
+        "impl": "reference", "metric": "Cheb-filter H·X nominal TFLOP/s", "value": val,
+        "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(slab), "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import paper_2504_00998_gb300 as fe
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = {"f32": fe.FE_F32, "f64": fe.FE_F64, "bf16": fe.FE_BF16_F32ACC,
+            "f32x3": fe.FE_F32_F32ACC}[args.prec]
+    dtype_name = {"f32": "f32", "f64": "f64", "bf16": "bf16", "f32x3": "f32"}[args.prec]
+    slab = workload(args.workload)
+    nvec, degree = slab.nvec, slab.degree
+    lib = fe.load()
+
+    m = fe.Mesh.from_slab(slab, device=local)
+    phi = torch.empty(m.n_phi, dtype=torch.float64, device=dev)
+    vb = torch.empty(m.n_psi, dtype=torch.float64, device=dev)
+    m.poisson_solve(slab.bias, rtol=POISSON_RTOL, phi=phi, vbare=vb)
+    m.set_potential(vb)
+    lo, hi = m.lanczos_bounds(torch.tensor(W.lanczos_start(m.n_psi), device=dev), LANCZOS_STEPS)
+    a0, b = lo, hi
+    a = a0 + R_FILTER * (b - a0)
+
+    X0 = torch.from_numpy(W.start_block(slab)).pin_memory()
+    X = torch.empty((m.n_psi, nvec), dtype=fe.storage_dtype(prec), device=dev)
+    X.copy_(X0.to(X.dtype) if X.dtype != X0.dtype else X0)
+    st = torch.cuda.current_stream(dev)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    marks = []
+
+    def step(rec):
+        e = [ev() for _ in range(5)] if rec else None
+        if rec:
+            e[0].record(st)
+        m.poisson_solve(slab.bias, rtol=POISSON_RTOL, phi=phi, vbare=vb)
+        if rec:
+            e[1].record(st)
+        m.set_potential(vb)
+        if rec:
+            e[2].record(st)
+        m.cheb_filter(X, degree, a, b, a0, prec=prec)
+        if rec:
+            e[3].record(st)
+        eig = m.rayleigh_ritz(X, prec=prec)
+        if rec:
+            e[4].record(st)
+            marks.append(e)
+        return eig
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    n0 = lib.fe_kernel_launches()
+    t_start, t_end = ev(), ev()
+    with ClockSampler(gpu_index(dev)) as clk:
+        t_start.record(st)
+        for _ in range(args.steps):
+            eig = step(True)
+        t_end.record(st)
+        torch.cuda.synchronize(dev)
+    launches = lib.fe_kernel_launches() - n0
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        lt = torch.tensor([launches], device=dev, dtype=torch.int64)
+        dist.all_reduce(lt)
+        launches = int(lt.item())
+        dist.barrier()
+    phase = np.zeros(4)
+    for e in marks:
+        phase += [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3]),
+                  e[3].elapsed_time(e[4])]
+    phase /= max(len(marks), 1)
+    ms_step = elapsed_ms / args.steps
+    flops_hx = nominal_flops_per_hx(slab, nvec)
+    flops_step = flops_hx * (degree + 1)
+    value = world * flops_step / (ms_step * 1e-3) / 1e12
+
+    # roofline of the dominant kernel: the fused Chebyshev operator launch
+    eb = 8 if prec == fe.FE_F64 else 4
+    n = m.n_psi
+    bytes_filter = (2 + 3 * (degree - 1)) * n * nvec * eb + degree * n * eb
+    bytes_per_launch = bytes_filter / degree
+    launch_ms = phase[2] / degree
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    kernel_key = {fe.FE_F32: "kron_f32_p5", fe.FE_F64: "kron_f64_p5"}.get(prec, "tc_p5")
+    traffic = traffic_record(kernel_key)
+
+    # end to end through the public API with host buffers: H2D of the start block, the
+    # step, D2H of the Ritz values
+    Xh = X0 if X.dtype == torch.float32 else X0.double().pin_memory()
+    eig_h = torch.empty(nvec, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize(dev)
+    e2e_start, e2e_end = ev(), ev()
+    e2e_start.record(st)
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        X.copy_(Xh, non_blocking=True)
+        eig = step(False)
+        eig_h.copy_(eig, non_blocking=True)
+    e2e_end.record(st)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e2e_start.elapsed_time(e2e_end) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = world * flops_step / (e2e_ms * 1e-3) / 1e12
+
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_fp64_compare and prec != fe.FE_F64:
+        # one cycle of both paths from the same start block: Ritz-value difference and the
+        # FP64 filter's throughput
+        Xm = torch.empty((n, nvec), dtype=fe.storage_dtype(prec), device=dev)
+        Xm.copy_(X0.to(Xm.dtype))
+        m.cheb_filter(Xm, degree, a, b, a0, prec=prec)
+        ev_m = m.rayleigh_ritz(Xm, prec=prec).cpu().numpy()
+        del Xm
+        Xd = X0.to(dev).double()
+        f0, f1 = ev(), ev()
+        f0.record(st)
+        m.cheb_filter(Xd, degree, a, b, a0, prec=fe.FE_F64)
+        f1.record(st)
+        ev_d = m.rayleigh_ritz(Xd, prec=fe.FE_F64).cpu().numpy()
+        torch.cuda.synchronize(dev)
+        fms = f0.elapsed_time(f1)
+        del Xd
+        k = min(int(slab.n_electrons // 2), nvec - 8)
+        extra = {"fp64_filter_ms": fms,
+                 "fp64_filter_tflops": flops_hx * degree / (fms * 1e-3) / 1e12,
+                 "eig_err_vs_fp64_ha": float(np.max(np.abs(ev_m[:k] - ev_d[:k]))),
+                 "eig_err_count": k}
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle(slab, nvec)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": "Cheb-filter H·X nominal TFLOP/s", "value": value, "unit": "TFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
+            "config": {"workload": workload_desc(slab),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (block of %.1f GB)" % (n * nvec * eb / 1e9),
+                       "filter_bounds": {"a0": a0, "a": a, "b": b}},
+            "phases_ms": {"poisson_and_veff": phase[0], "set_potential": phase[1],
+                          "cheb_filter": phase[2], "cholqr_rr": phase[3]},
+            "filter_tflops": flops_hx * degree / (phase[2] * 1e-3) / 1e12,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_src, "kernel": kernel_key,
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "launch_ms": launch_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": int(X0.numel() * X.element_size()),
+                    "d2h_bytes_per_step": int(nvec * 8)},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        line.update(extra)
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    m.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * fe.h -- C ABI of libfe, a GB300 (sm_103a) library for the data-parallel hot path of
+ * real-space finite-element Kohn-Sham DFT for slabs under an external potential bias
+ * (Ramakrishnan, Sai Gautam, Motamarri, "Real-space methods for ab initio modeling of
+ * surfaces and interfaces under external potential bias").
+ *
+ * Discrete problem (Section 2.3, FE discretization): C0 Lagrange elements of degree p on
+ * GLL nodes over a uniform hexahedral mesh of the box [0,Lx) x [0,Ly) x [0,Lz], periodic
+ * in x and y.  The Kohn-Sham eigenproblem H u = eps M u (Section 2.3) is handled in the
+ * symmetric standard form  Ht = M^-1/2 H M^-1/2 = 1/2 M^-1/2 K M^-1/2 + diag(V_eff),
+ * K_IJ = int grad N_I . grad N_J (Section 2.3), M the GLL-lumped overlap, V_eff collocated
+ * at the nodes (Eq. Veff and Hloc; the exchange-correlation term is not part of this
+ * library).  The Poisson problem -1/(4 pi) Lap phi = rho + b (Eq. Poissons equation) is
+ * K phi = 4 pi c, c_I = M_II (rho + b)(x_I), with the bias setups of Section 2.2:
+ * CEF (Eq. governing_equations CEF) and CPD / L-CPD (Eq. governing_equations APD).
+ *
+ * Node numbering.  Global node (gx, gy, gz), gx in [0, nx p), gy in [0, ny p),
+ * gz in [0, nz p]; node coordinate along an axis with cell size h: (g / p) h +
+ * (xi_{g mod p} + 1) h / 2 with xi the GLL points on [-1, 1].
+ *   phi node id = gx + NX (gy + NY gz)                    (NX = nx p, NY = ny p)
+ *   psi node id = gx + NX (gy + NY (gz - gz_lo))          gz_lo = 1 if the bottom psi face
+ *                 is homogeneous Dirichlet, else 0; the top Dirichlet face drops gz = nz p.
+ *
+ * Conventions for every call:
+ *   - All arrays are owned by the caller and are never freed by the library.  Arrays
+ *     named *_dev are device pointers on the mesh's device; *_host are host pointers.
+ *   - Wavefunction blocks are node-major with the vectors contiguous: element (node i,
+ *     vector j) is at X[i * ld + j], 0 <= j < nvec <= ld.  FE_F64 blocks are double,
+ *     all other precisions use float storage.  X must be 16-byte aligned and
+ *     ld * sizeof(element) must be a multiple of 16 bytes.
+ *   - Work is enqueued on the mesh's stream in order.  Calls that return host scalars
+ *     (info structs, bounds) synchronise that stream; the others do not.
+ *   - Errors are reported as status codes, never by aborting; fe_last_error() gives a
+ *     thread-local message for the last non-FE_OK status.  Arguments are validated on
+ *     the host before anything is enqueued; a failing call leaves outputs unspecified.
+ *   - Iterative device loops carry an iteration cap and report FE_ENOCONV; no device
+ *     code waits without a bound.
+ */
+#ifndef FE_H
+#define FE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FE_OK = 0,
+  FE_EINVAL = 1,        /* invalid argument (null pointer, bad size, misalignment)     */
+  FE_ENOMEM = 2,        /* device allocation failed                                     */
+  FE_ECUDA = 3,         /* a CUDA / cuBLAS / cuSOLVER call failed                       */
+  FE_ENOCONV = 4,       /* an iteration hit its cap before the tolerance                */
+  FE_EBREAKDOWN = 5,    /* Cholesky of a Gram matrix failed (not positive definite)     */
+  FE_ETIMEOUT = 6,      /* reserved: a bounded device wait expired                      */
+  FE_EUNSUPPORTED = 7   /* valid request that this build does not implement             */
+} fe_status;
+
+/* Arithmetic of the Hamiltonian application.
+ *   FE_F64          double storage, double sum-factorised products (exact path).
+ *   FE_F32          float storage, float sum-factorised products, float accumulation.
+ *   FE_BF16_F32ACC  float storage, per-cell dense stiffness products with bf16 operands
+ *                   on the tcgen05 tensor cores, float accumulation in tensor memory.
+ *   FE_F32_F32ACC   float storage, per-cell dense products with the float operands split
+ *                   into bf16 high and low parts on tcgen05, float accumulation.        */
+typedef enum { FE_F64 = 0, FE_F32 = 1, FE_BF16_F32ACC = 2, FE_F32_F32ACC = 3 } fe_precision;
+
+/* Wavefunction boundary condition on a z face (x and y are always periodic). */
+typedef enum { FE_FACE_NEUMANN = 0, FE_FACE_DIRICHLET = 1 } fe_face_bc;
+
+typedef struct fe_mesh fe_mesh; /* opaque, library-owned */
+
+typedef struct {
+  double L[3];            /* box lengths Lx, Ly, Lz (bohr), > 0                       */
+  int ncell[3];           /* cells per direction, >= 1                                  */
+  int p;                  /* polynomial degree, 1 <= p <= 6                              */
+  fe_face_bc psi_z[2];    /* psi condition on the z = 0 and z = Lz faces                 */
+  int device;             /* CUDA device ordinal                                         */
+  void* stream;           /* cudaStream_t for all work of this mesh (NULL = legacy)      */
+} fe_mesh_desc;
+
+/* Create a mesh (Section 2.3).  Builds the 1D GLL rules and element matrices on the host
+ * and uploads the node tables.  *out receives a handle owned by the library. */
+fe_status fe_mesh_create(const fe_mesh_desc* desc, fe_mesh** out);
+fe_status fe_mesh_destroy(fe_mesh* mesh);
+fe_status fe_mesh_info(const fe_mesh* mesh, int64_t* n_phi, int64_t* n_psi, int64_t* n_cells);
+/* Replace the stream used by all later calls on this mesh. */
+fe_status fe_mesh_set_stream(fe_mesh* mesh, void* stream);
+
+/* Node coordinates in phi order, xyz_dev[n_phi][3] (Section 2.3 node layout). */
+fe_status fe_node_coords(const fe_mesh* mesh, double* xyz_dev);
+/* Diagonal of the GLL-lumped overlap M on phi nodes, m_dev[n_phi]. */
+fe_status fe_lumped_mass(const fe_mesh* mesh, double* m_dev);
+
+/* Pseudo-atoms (Eq. Governing equations1): positions R_host[n][3] (bohr) and valence
+ * charges Z_host[n].  Defines V_loc^a = -Z erf(r/rc_loc)/r, the smeared nuclear charge
+ * b^a = -Z g_{sigma_b} (g_s a normalised Gaussian of standard deviation s) with
+ * V_sm^a = -Z erf(r/(sqrt2 sigma_b))/r, and the model electron density
+ * rho = sum_a Z_a g_{sigma_rho}.  Periodic x/y images are summed; every atom-centred
+ * function is cut at 10 bohr.  b^a is renormalised per atom and rho globally so that
+ * their lumped integrals are exactly -Z_a and sum Z_a.  The arrays are copied. */
+fe_status fe_set_atoms(fe_mesh* mesh, int n, const double* R_host, const double* Z_host,
+                       double sigma_b, double rc_loc, double sigma_rho);
+
+/* V_eff at psi nodes, veff_dev[n_psi] (Eq. Veff and Hloc without exchange-correlation:
+ * V_eff = phi + V_loc - V_sm + V_app).  Copied into the mesh. */
+fe_status fe_set_potential(fe_mesh* mesh, const double* veff_dev);
+
+/* Y = Ht X (Eq. Veff and Hloc, Section 2.3).  X, Y [n_psi][ld], nvec vectors; X and Y
+ * must not overlap.  Needs fe_set_potential first. */
+fe_status fe_apply_H(fe_mesh* mesh, const void* X, void* Y, int64_t nvec, int64_t ld,
+                     fe_precision prec);
+
+/* In-place degree-m scaled Chebyshev filter of X (Zhou & Saad three-term recurrence):
+ * X <- T_m((Ht - c)/e) X / T_m((a0 - c)/e), e = (b - a)/2, c = (b + a)/2, a0 < a < b;
+ * degree counts applications of Ht.  Uses one library-owned workspace of X's size. */
+fe_status fe_cheb_filter(fe_mesh* mesh, void* X, int64_t nvec, int64_t ld, int degree,
+                         double a, double b, double a0, fe_precision prec);
+
+typedef enum { FE_BIAS_CEF = 0, FE_BIAS_CPD = 1 } fe_bias_kind;
+
+typedef struct {
+  fe_bias_kind kind;
+  double field;               /* CEF: E (Ha/bohr); V_app has slope -E on [0.1Lz, 0.9Lz]    */
+  double dV, zA, zB;          /* CPD: phi_tilde = 0 for z <= zA, dV for z >= zB            */
+  int has_patch;              /* L-CPD: restrict the z >= zB set to the patch below        */
+  double patch_lo[2], patch_hi[2];
+  double rtol;                /* relative residual target of the CG, e.g. 1e-10            */
+  int max_iter;               /* CG iteration cap                                          */
+} fe_poisson_bc;
+
+typedef struct { int iters; double rel_residual; int status; } fe_solve_info;
+
+/* Solve the Poisson problem with the bias setup in *bc (Eq. governing_equations CEF /
+ * APD) by Jacobi-preconditioned CG on the matrix-free operator.
+ *   rho_dev   electron density at phi nodes [n_phi], or NULL for the atoms' model density
+ *             (fe_set_atoms is required in both cases for b and V_loc - V_sm).
+ *   phi_dev   output potential phi at phi nodes [n_phi]; CEF: sum M phi = 0.
+ *   vbare_dev optional output [n_psi]: phi + V_loc - V_sm + V_app at psi nodes, i.e. the
+ *             V_eff of this library (Section 3.2 calls it V_bare).
+ *   info      optional: iterations, final relative residual, status.
+ * Returns FE_ENOCONV if max_iter is reached first. */
+fe_status fe_poisson_solve(fe_mesh* mesh, const double* rho_dev, const fe_poisson_bc* bc,
+                           double* phi_dev, double* vbare_dev, fe_solve_info* info);
+
+/* Same solve for a given load f_dev [n_phi] (K phi = f on the free nodes) instead of
+ * 4 pi M (rho + b).  CPD / L-CPD: constrained nodes take phic_dev [n_phi] (read on the
+ * constrained set only), or the physical values -(V_loc - V_sm) / dV - (V_loc - V_sm) when
+ * phic_dev is NULL.  CEF: the load is projected and sum M phi = 0 as above.  This is also
+ * the adjoint solve: K is symmetric, so the gradient of a loss L(phi) with respect to f is
+ * the solution for the load dL/dphi with zero constrained values. */
+fe_status fe_poisson_solve_load(fe_mesh* mesh, const double* f_dev, const fe_poisson_bc* bc,
+                                const double* phic_dev, double* phi_dev, fe_solve_info* info);
+
+/* The constrained node set of bc (Eq. governing_equations APD; empty for CEF) as a byte
+ * mask_dev [n_phi] (1 = constrained) and the physical constrained values values_dev
+ * [n_phi] (-(V_loc - V_sm) on Omega_0, dV - (V_loc - V_sm) on Omega_1, 0 elsewhere). */
+fe_status fe_poisson_constraints(fe_mesh* mesh, const fe_poisson_bc* bc, unsigned char* mask_dev,
+                                 double* values_dev);
+
+/* y = K x on phi nodes (Section 2.3), x, y [n_phi] doubles; no constraints applied. */
+fe_status fe_poisson_apply_K(fe_mesh* mesh, const double* x_dev, double* y_dev);
+
+/* Poisson load 4 pi M (rho + b) at phi nodes [n_phi] for the atoms (rho_dev NULL) or the
+ * given density; f_dev [n_phi]; rho_out_dev / b_out_dev optional [n_phi] copies. */
+fe_status fe_poisson_rhs(fe_mesh* mesh, const double* rho_dev, double* f_dev,
+                         double* rho_out_dev, double* b_out_dev);
+
+/* Orthonormalise X (Cholesky-QR, repeated; shifted Cholesky-QR3 when the first Gram is
+ * ill-conditioned) and rotate it to the Ritz vectors of Ht: X <- X Q, eig_dev[nvec]
+ * ascending Ritz values.  Gram matrices, the projected matrix and the rotation are
+ * computed in double precision whatever the storage; float blocks are promoted to a
+ * library-owned double workspace.  prec selects the arithmetic of the one Ht X product. */
+fe_status fe_rayleigh_ritz(fe_mesh* mesh, void* X, int64_t nvec, int64_t ld, double* eig_dev,
+                           fe_precision prec);
+
+/* Copies of the atom fields at phi nodes [n_phi] (any output may be NULL): the model
+ * density rho, the smeared nuclear charge b and V_loc - V_sm (see fe_set_atoms). */
+fe_status fe_atom_fields(fe_mesh* mesh, double* rho_dev, double* b_dev, double* vlms_dev);
+
+/* Electrostatic energy of the slab at fixed density for the potential phi_dev [n_phi]
+ * returned by fe_poisson_solve with the same bc (Eq. electrostatics Energy, Eq. local
+ * pseudopotential and the V_app term of Eq. KS DFT variational problem cef, lumped
+ * quadrature; self energy excluded):
+ *   E = c.phi - phi^T K phi / (8 pi) + sum M (V_loc - V_sm) rho + sum M (rho + b) V_app.
+ * Because phi maximises E over the free nodes, the derivatives are explicit: *dE_dfield
+ * (CEF, = -dipole when all charge lies on the linear part of V_app), *dE_ddV (CPD, the
+ * reaction charge on Omega_1), and the node fields g_rho_dev, g_b_dev, g_vlms_dev [n_phi]
+ * = dE/d rho, dE/d b, dE/d (V_loc - V_sm) for fe_atom_fields_vjp.  Synchronises. */
+fe_status fe_energy(fe_mesh* mesh, const fe_poisson_bc* bc, const double* phi_dev, double* E_host,
+                    double* dE_dfield_host, double* dE_ddV_host, double* g_rho_dev,
+                    double* g_b_dev, double* g_vlms_dev);
+
+/* Vector-Jacobian product of the atom fields with respect to the positions:
+ * dR_host[a][k] = sum_I g_rho_I d rho_I / dR_ak + g_b_I d b_I / dR_ak
+ *                 + g_vlms_I d (V_loc - V_sm)_I / dR_ak,
+ * analytic, including the per-atom and global renormalisations of fe_set_atoms.
+ * Synchronises. */
+fe_status fe_atom_fields_vjp(fe_mesh* mesh, const double* g_rho_dev, const double* g_b_dev,
+                             const double* g_vlms_dev, double* dR_host);
+
+/* k-step Lanczos on Ht from the start vector v0_dev[n_psi] (Zhou & Li bounds):
+ * *lo = smallest Ritz value, *hi = largest Ritz value + ||f_k||.  Synchronises. */
+fe_status fe_lanczos_bounds(fe_mesh* mesh, const double* v0_dev, int steps, double* lo,
+                            double* hi);
+
+/* Number of this library's own CUDA kernels enqueued since it was loaded (replays of its
+ * internal CUDA graphs included; cuBLAS / cuSOLVER kernels excluded).  Instrumentation for
+ * benchmarks; process-wide, never reset. */
+int64_t fe_kernel_launches(void);
+
+/* Thread-local message describing the last non-FE_OK status on this thread. */
+const char* fe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FE_H */

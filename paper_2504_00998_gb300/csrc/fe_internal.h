@@ -1,0 +1,166 @@
+// Internal declarations of libfe (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/fe.h"
+
+#define FE_MAXP 6
+#define FE_MAXN1 (FE_MAXP + 1)
+
+// ---- error state ------------------------------------------------------------------------
+fe_status fe_fail(fe_status st, const char* fmt, ...);
+
+// ---- instrumentation: number of this library's kernels enqueued (graph replays included) ----
+void fe_count_launch(int64_t n = 1);
+
+#define FE_CUDA(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return (cudaGetLastError(),                                                      \
+              fe_fail(FE_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,             \
+                      cudaGetErrorString(e_)));                                        \
+  } while (0)
+
+#define FE_CUBLAS(call)                                                                \
+  do {                                                                                 \
+    cublasStatus_t s_ = (call);                                                        \
+    if (s_ != CUBLAS_STATUS_SUCCESS)                                                   \
+      return fe_fail(FE_ECUDA, "%s:%d %s: cublas status %d", __FILE__, __LINE__, #call, \
+                     (int)s_);                                                         \
+  } while (0)
+
+#define FE_CUSOLVER(call)                                                              \
+  do {                                                                                 \
+    cusolverStatus_t s_ = (call);                                                      \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                 \
+      return fe_fail(FE_ECUDA, "%s:%d %s: cusolver status %d", __FILE__, __LINE__,     \
+                     #call, (int)s_);                                                  \
+  } while (0)
+
+#define FE_TRY(expr)                  \
+  do {                                \
+    fe_status t_ = (expr);            \
+    if (t_ != FE_OK) return t_;       \
+  } while (0)
+
+// ---- tensor-product operator arguments ----------------------------------------------------
+// The assembled stiffness of the tensor-product mesh is
+//   K = ax K1 (x) M1 (x) M1 + ay M1 (x) K1 (x) M1 + az M1 (x) M1 (x) K1   (x (x) y (x) z),
+// with K1, M1 the exact 1D reference element matrices assembled along each axis, and the
+// lumped overlap is M = J mx (x) my (x) mz.  The operator kernel applies
+//   Y = alpha (oscale * K (S X) + (V - c) X) + beta Z,  S = diag(input scale),
+// sweeping z.  Coefficient tables carry the per-local-index input scales.
+struct KronCoef {
+  // in-plane: y contraction (a = Ay_M U, b = Ay_K U) then x contraction
+  // (W1 = Ax_M a, W2 = Ax_K a + Ax_M b); rows = output local index, cols = input local index
+  double AyM[FE_MAXN1][FE_MAXN1], AyK[FE_MAXN1][FE_MAXN1];
+  double AxM[FE_MAXN1][FE_MAXN1], AxK[FE_MAXN1][FE_MAXN1];
+  // z contraction (cell-local): acc[j] += AzK[j][k] W1 + AzM[j][k] W2
+  double AzK[FE_MAXN1][FE_MAXN1], AzM[FE_MAXN1][FE_MAXN1];
+  double sig[FE_MAXN1];   // per-local-index in-plane output scale factor (x and y)
+  double wz[FE_MAXN1];    // GLL weights (for the z mass factor of a plane)
+  double zin;             // J^-1/2 (or 1 for the Poisson operator)
+  double zout;            // 1/2 J^-1/2 (or 1)
+  int mass_scale;         // 1: Hamiltonian (mass-scaled), 0: plain K
+};
+
+struct KronGeom {
+  int p, NX, NY, nz;      // nodes per periodic row, cells in z
+  int gz_lo, NZs;         // first stored plane, number of stored planes
+  int bx, by, zseg;       // cells per block in x, y; layers per z segment
+  int nbx, nby;           // blocks in x, y
+};
+
+template <typename T>
+struct KronIO {
+  const T* X; int64_t ldx;
+  T* Y; int64_t ldy;
+  const T* Z; int64_t ldz;   // previous Chebyshev iterate (nullptr: beta ignored)
+  const T* V;                // potential per stored node (nullptr: none)
+  int64_t nvec;
+  T alpha, beta, shift;      // Y = alpha (H - shift) X + beta Z
+};
+
+struct KronTile { int bx, by, zseg, nch; };
+
+// operator launchers: double with 16-byte chunks, float with 16-byte chunks, and double
+// with one element per node (single-vector Poisson operator)
+namespace fe {
+fe_status kron_f64(const KronCoef& cf, const KronGeom& g, const KronIO<double>& io, int nch,
+                   cudaStream_t st);
+fe_status kron_f32(const KronCoef& cf, const KronGeom& g, const KronIO<float>& io, int nch,
+                   cudaStream_t st);
+fe_status kron_k1(const KronCoef& cf, const KronGeom& g, const KronIO<double>& io, int nch,
+                  cudaStream_t st);
+}  // namespace fe
+
+// ---- the mesh ---------------------------------------------------------------------------
+struct fe_mesh {
+  fe_mesh_desc desc;
+  int p, nx, ny, nz;
+  int NX, NY, NZ;          // NZ = nz p + 1 phi planes
+  int gz_lo, gz_hi, NZs;   // stored psi planes
+  int64_t n_phi, n_psi, n_cells;
+  double h[3], J;
+  double xi[FE_MAXN1], w[FE_MAXN1];
+  double K1[FE_MAXN1][FE_MAXN1], M1[FE_MAXN1][FE_MAXN1];
+  cudaStream_t stream;
+  int device;
+  cudaStream_t aux_stream = nullptr;   // library-owned, non-blocking: graph capture
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
+  KronCoef coefH;          // Hamiltonian (mass-scaled, 1/2 factor)
+  KronCoef coefK;          // plain stiffness
+
+  double* d_veff = nullptr;   // [n_psi]
+  float* d_veff_f = nullptr;  // [n_psi]
+  bool has_potential = false;
+
+  int natoms = 0;
+  double* d_atoms = nullptr;  // [natoms][4] = x, y, z, Z
+  double* h_atoms = nullptr;
+  double sigma_b = 0.5, rc_loc = 1.0, sigma_rho = 1.0;
+  double* d_vlms = nullptr;   // V_loc - V_sm at phi nodes
+  double* d_rho = nullptr;    // model density at phi nodes (renormalised)
+  double* d_b = nullptr;      // smeared nuclear charge at phi nodes (renormalised)
+  double* d_mass = nullptr;   // lumped mass at phi nodes
+  double rho_scale = 1.0;     // rho = rho_scale * sum_a Z_a g_{sigma_rho}
+  double n_electrons = 0.0;
+
+  // workspaces (grown on demand, freed with the mesh)
+  void* ws[10] = {nullptr};
+  size_t ws_bytes[10] = {0};
+
+  // tensor-core path: p of the uploaded cell-matrix image, pinned wait-expiry flag
+  int tc_img_p = -1;
+  int* tc_err_pinned = nullptr;
+
+  cublasHandle_t cublas = nullptr;
+  cusolverDnHandle_t cusolver = nullptr;
+
+  // tile choices per (precision, nvec-bucket), filled by the tuner
+  KronTile tileH[4];
+  bool tuned[4] = {false, false, false, false};
+  KronTile tileK;
+};
+
+enum { WS_CHEB = 0, WS_RR_X = 1, WS_RR_HX = 2, WS_RR_SMALL = 3, WS_CG = 4, WS_RED = 5,
+       WS_LANCZOS = 6, WS_TC = 7, WS_TC_IMG = 8, WS_YCELL = 9 };
+
+fe_status fe_ws(fe_mesh* m, int slot, size_t bytes, void** out);
+fe_status fe_activate(const fe_mesh* m);
+KronGeom fe_geom(const fe_mesh* m, bool psi, const KronTile& t);
+KronTile fe_default_tile(const fe_mesh* m, bool psi, int elem_bytes, int64_t nvec);
+
+// fields (potentials, densities) -- fe_fields.cu
+fe_status fe_fields_build(fe_mesh* m);
+// deterministic reductions -- fe_blas.cu
+fe_status fe_dot(fe_mesh* m, const double* x, const double* y, int64_t n, double* out_dev);

@@ -1,0 +1,547 @@
+// Poisson problem with the paper's two bias setups, solved by Jacobi-preconditioned CG on
+// the matrix-free stiffness operator.
+//
+// Eq. Poissons equation, FE form (Section 2.3): K phi = 4 pi c, c_I = M_II (rho + b)(x_I).
+// CEF (Eq. governing_equations CEF): zero-Neumann z faces (natural), int phi = 0.  The load
+//   is projected onto range(K) (f <- f - (sum f / sum M) M), the CG residual is re-projected
+//   onto the complement of the constants every iteration, and phi is shifted to
+//   sum_I M_I phi_I = 0 at the end.  V_app is the sawtooth of Section 2.2.1 with slope -E on
+//   [0.1 Lz, 0.9 Lz] (extrema 0.1 fractional units from the boundaries, Section 3.1) and
+//   linear return ramps to zero at z = 0 and z = Lz.
+// CPD / L-CPD (Eq. governing_equations APD): phi = -(V_loc - V_sm) on Omega_0 = {z <= zA}
+//   and dV - (V_loc - V_sm) on Omega_1 = {z >= zB} (intersected with the patch for L-CPD);
+//   CG runs on the free nodes with the constrained rows and columns masked; V_app = 0.
+//
+// Every CG iteration is a fixed sequence of stream-ordered launches with all scalars on the
+// device; a block of iterations is captured once into a CUDA graph and replayed, and the
+// host reads the convergence flag between replays.  The iteration cap bounds the loop.
+#include <cmath>
+#include <vector>
+
+#include "fe_blas.cuh"
+#include "fe_internal.h"
+
+namespace {
+
+constexpr double FOUR_PI = 12.566370614359172;
+
+struct CgState {
+  double rz, rz_new, pq, rr, alpha, beta, bnorm2, tol2, mean;
+  int done, iters, maxit;
+};
+
+struct PGeom {
+  int NX, NY, NZ, p;
+  double hx, hy, hz, Lz;
+  double xi[FE_MAXN1];
+  double K1d0, K1dp;            // K1[0][0], K1[p][p]
+  double K1diag[FE_MAXN1], M1diag[FE_MAXN1];
+  double ax, ay, az;
+};
+
+__device__ __forceinline__ void pnode(const PGeom& g, int64_t id, int* gx, int* gy, int* gz) {
+  *gx = (int)(id % g.NX);
+  *gy = (int)((id / g.NX) % g.NY);
+  *gz = (int)(id / ((int64_t)g.NX * g.NY));
+}
+
+__device__ __forceinline__ double zcoord(const PGeom& g, int gz) {
+  return (gz / g.p) * g.hz + (g.xi[gz % g.p] + 1.0) * 0.5 * g.hz;
+}
+
+// diagonal of an assembled 1D element matrix at global index gi (periodic or bounded)
+__device__ __forceinline__ double diag1(const double* d, int p, int gi, bool periodic, int nmax) {
+  int l = gi % p;
+  if (l != 0) return d[l];
+  if (periodic) return d[0] + d[p];
+  if (gi == 0) return d[0];
+  if (gi == nmax) return d[p];
+  return d[0] + d[p];
+}
+
+__device__ __forceinline__ double vapp(double z, double E, double Lz) {
+  const double z1 = 0.1 * Lz, z2 = 0.9 * Lz;
+  if (z < z1) return -E * (z1 - 0.5 * Lz) * z / z1;
+  if (z > z2) return -E * (z2 - 0.5 * Lz) * (Lz - z) / (Lz - z2);
+  return -E * (z - 0.5 * Lz);
+}
+
+// f = 4 pi M (rho + b); Jacobi inverse; constraint mask and values; phi initialisation
+// (f_ext: a given load instead of 4 pi M (rho + b); phic_ext: given constrained values)
+__global__ void k_setup(PGeom g, fe_poisson_bc bc, const double* __restrict__ mass,
+                        const double* __restrict__ rho, const double* __restrict__ b,
+                        const double* __restrict__ vlms, const double* __restrict__ f_ext,
+                        const double* __restrict__ phic_ext, double* __restrict__ f,
+                        double* __restrict__ dinv, unsigned char* __restrict__ mask,
+                        double* __restrict__ phi, int64_t n) {
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < n;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    int gx, gy, gz;
+    pnode(g, id, &gx, &gy, &gz);
+    f[id] = f_ext ? f_ext[id] : FOUR_PI * mass[id] * (rho[id] + b[id]);
+    int nz = g.NZ - 1;
+    double kx = diag1(g.K1diag, g.p, gx, true, 0), mx = diag1(g.M1diag, g.p, gx, true, 0);
+    double ky = diag1(g.K1diag, g.p, gy, true, 0), my = diag1(g.M1diag, g.p, gy, true, 0);
+    double kz = diag1(g.K1diag, g.p, gz, false, nz), mz = diag1(g.M1diag, g.p, gz, false, nz);
+    double d = g.ax * kx * my * mz + g.ay * mx * ky * mz + g.az * mx * my * kz;
+    dinv[id] = 1.0 / d;
+    unsigned char c = 0;
+    double val = 0.0;
+    if (bc.kind == FE_BIAS_CPD) {
+      double x = (gx / g.p) * g.hx + (g.xi[gx % g.p] + 1.0) * 0.5 * g.hx;
+      double y = (gy / g.p) * g.hy + (g.xi[gy % g.p] + 1.0) * 0.5 * g.hy;
+      double z = zcoord(g, gz);
+      const double tol = 1e-12;
+      bool om0 = z <= bc.zA + tol;
+      bool om1 = z >= bc.zB - tol;
+      if (bc.has_patch)
+        om1 = om1 && x >= bc.patch_lo[0] - tol && x <= bc.patch_hi[0] + tol &&
+              y >= bc.patch_lo[1] - tol && y <= bc.patch_hi[1] + tol;
+      if (om0) { c = 1; val = phic_ext ? phic_ext[id] : -vlms[id]; }
+      if (om1) { c = 1; val = phic_ext ? phic_ext[id] : bc.dV - vlms[id]; }
+    }
+    mask[id] = c;
+    phi[id] = val;
+  }
+}
+
+// partial sums of x (y == nullptr) or x.y; one partial per block
+__global__ void k_psum(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
+                       double* __restrict__ part) {
+  __shared__ double sh[fe::RED_THREADS];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
+       i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS)
+    s += y ? x[i] * y[i] : x[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__device__ double block_sum_partials(const double* part) {
+  __shared__ double sh[fe::RED_BLOCKS];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < fe::RED_BLOCKS; i += blockDim.x) s += part[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// CEF load projection: f <- f - (sum f / sum M) M
+__global__ void k_fin_project_load(const double* part_f, const double* part_m, CgState* s) {
+  double sf = block_sum_partials(part_f);
+  double sm = block_sum_partials(part_m);
+  if (threadIdx.x == 0) s->mean = sf / sm;
+}
+__global__ void k_project_load(double* __restrict__ f, const double* __restrict__ mass,
+                               const CgState* s, int64_t n) {
+  double c = s->mean;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    f[i] -= c * mass[i];
+}
+
+// r = (f - K phi) on free rows, 0 on constrained rows
+__global__ void k_resid0(const double* __restrict__ f, const double* __restrict__ kphi,
+                         const unsigned char* __restrict__ mask, double* __restrict__ r,
+                         int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = mask[i] ? 0.0 : f[i] - kphi[i];
+}
+
+__global__ void k_fin_mean(const double* part, CgState* s, double inv_n) {
+  double v = block_sum_partials(part);
+  if (threadIdx.x == 0) s->mean = v * inv_n;
+}
+
+// r -= mean (CEF only); z = Dinv r on free rows; one partial of r.z and r.r per block
+__global__ void k_precond(double* __restrict__ r, double* __restrict__ z,
+                          const double* __restrict__ dinv, const unsigned char* __restrict__ mask,
+                          const CgState* s, int project, int64_t n, double* __restrict__ part_rz,
+                          double* __restrict__ part_rr) {
+  __shared__ double sh1[fe::RED_THREADS], sh2[fe::RED_THREADS];
+  double mean = project ? s->mean : 0.0;
+  double a1 = 0.0, a2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
+       i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS) {
+    double ri = r[i];
+    if (project) { ri -= mean; r[i] = ri; }
+    double zi = mask[i] ? 0.0 : dinv[i] * ri;
+    z[i] = zi;
+    a1 += ri * zi;
+    a2 += ri * ri;
+  }
+  sh1[threadIdx.x] = a1;
+  sh2[threadIdx.x] = a2;
+  __syncthreads();
+  for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) { sh1[threadIdx.x] += sh1[threadIdx.x + w]; sh2[threadIdx.x] += sh2[threadIdx.x + w]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { part_rz[blockIdx.x] = sh1[0]; part_rr[blockIdx.x] = sh2[0]; }
+}
+
+// first iteration: p = z, rz, rr, |b|^2
+__global__ void k_fin_init(const double* part_rz, const double* part_rr, CgState* s, double rtol) {
+  double rz = block_sum_partials(part_rz);
+  double rr = block_sum_partials(part_rr);
+  if (threadIdx.x == 0) {
+    s->rz = rz;
+    s->rr = rr;
+    s->bnorm2 = rr;
+    s->tol2 = rtol * rtol * rr;
+    s->done = (rr <= s->tol2) || rr == 0.0;
+    s->iters = 0;
+  }
+}
+
+__global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+// alpha = rz / p.q
+__global__ void k_fin_alpha(const double* part, CgState* s) {
+  double pq = block_sum_partials(part);
+  if (threadIdx.x == 0) {
+    s->pq = pq;
+    s->alpha = (s->done || pq == 0.0) ? 0.0 : s->rz / pq;
+  }
+}
+
+// x += alpha p; r -= alpha q (free rows); partial sums of r for the projection
+__global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r,
+                            const double* __restrict__ p, const double* __restrict__ q,
+                            const unsigned char* __restrict__ mask, const CgState* s, int64_t n,
+                            double* __restrict__ part) {
+  __shared__ double sh[fe::RED_THREADS];
+  double a = s->alpha;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
+       i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS) {
+    double ri = r[i];
+    if (!mask[i]) {
+      x[i] += a * p[i];
+      ri -= a * q[i];
+      r[i] = ri;
+    }
+    acc += ri;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// beta = rz_new / rz; convergence test on |r|^2; iteration count
+__global__ void k_fin_beta(const double* part_rz, const double* part_rr, CgState* s) {
+  double rz = block_sum_partials(part_rz);
+  double rr = block_sum_partials(part_rr);
+  if (threadIdx.x == 0) {
+    if (!s->done) {
+      s->beta = s->rz == 0.0 ? 0.0 : rz / s->rz;
+      s->rz = rz;
+      s->rr = rr;
+      s->iters += 1;
+      if (rr <= s->tol2 || s->iters >= s->maxit) s->done = 1;
+    } else {
+      s->beta = 0.0;
+    }
+  }
+}
+
+// p = z + beta p (skipped once converged so p, x stay fixed)
+__global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z, const CgState* s,
+                           int64_t n) {
+  if (s->done && s->alpha == 0.0) return;
+  double b = s->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + b * p[i];
+}
+
+// CEF: phi -= (M . phi) / sum M
+__global__ void k_shift_mean(double* __restrict__ phi, const double* part_mphi,
+                             const double* part_m, int64_t n) {
+  __shared__ double c;
+  double a = block_sum_partials(part_mphi);
+  double b = block_sum_partials(part_m);
+  if (threadIdx.x == 0) c = a / b;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    phi[i] -= c;
+}
+
+// V_eff at psi nodes: phi + (V_loc - V_sm) + V_app
+__global__ void k_vbare(PGeom g, const double* __restrict__ phi, const double* __restrict__ vlms,
+                        double field, int cef, int gz_lo, double* __restrict__ out, int64_t npsi) {
+  int64_t off = (int64_t)gz_lo * g.NX * g.NY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npsi;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t id = i + off;
+    int gz = (int)(id / ((int64_t)g.NX * g.NY));
+    double v = phi[id] + vlms[id];
+    if (cef) v += vapp(zcoord(g, gz), field, g.Lz);
+    out[i] = v;
+  }
+}
+
+PGeom make_geom(const fe_mesh* m) {
+  PGeom g;
+  g.NX = m->NX; g.NY = m->NY; g.NZ = m->NZ; g.p = m->p;
+  g.hx = m->h[0]; g.hy = m->h[1]; g.hz = m->h[2];
+  g.Lz = m->desc.L[2];
+  for (int k = 0; k < FE_MAXN1; ++k) {
+    g.xi[k] = k <= m->p ? m->xi[k] : 0.0;
+    g.K1diag[k] = k <= m->p ? m->K1[k][k] : 0.0;
+    g.M1diag[k] = k <= m->p ? m->M1[k][k] : 0.0;
+  }
+  g.ax = m->h[1] * m->h[2] / (2.0 * m->h[0]);
+  g.ay = m->h[0] * m->h[2] / (2.0 * m->h[1]);
+  g.az = m->h[0] * m->h[1] / (2.0 * m->h[2]);
+  return g;
+}
+
+}  // namespace
+
+extern "C" fe_status fe_poisson_rhs(fe_mesh* m, const double* rho, double* f, double* rho_out,
+                                    double* b_out) {
+  if (!m || !f) return fe_fail(FE_EINVAL, "fe_poisson_rhs: null argument");
+  if (!m->d_rho) return fe_fail(FE_EINVAL, "fe_poisson_rhs: call fe_set_atoms first");
+  FE_TRY(fe_activate(m));
+  const int64_t n = m->n_phi;
+  const double* r = rho ? rho : m->d_rho;
+  // reuse the setup kernel's load computation through a scratch mask / dinv
+  void* wsp;
+  FE_TRY(fe_ws(m, WS_CG, n * (sizeof(double) * 2 + 1) + 64, &wsp));
+  double* dinv = (double*)wsp;
+  double* phi = dinv + n;
+  unsigned char* mask = (unsigned char*)(phi + n);
+  fe_poisson_bc bc = {};
+  bc.kind = FE_BIAS_CEF;
+  k_setup<<<fe::grid_for(n), 256, 0, m->stream>>>(make_geom(m), bc, m->d_mass, r, m->d_b,
+                                                   m->d_vlms, nullptr, nullptr, f, dinv, mask,
+                                                   phi, n); fe_count_launch();
+  if (rho_out) FE_CUDA(cudaMemcpyAsync(rho_out, r, n * 8, cudaMemcpyDeviceToDevice, m->stream));
+  if (b_out) FE_CUDA(cudaMemcpyAsync(b_out, m->d_b, n * 8, cudaMemcpyDeviceToDevice, m->stream));
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisson_bc* bc,
+                                  double* phi, double* vbare, fe_solve_info* info,
+                                  bool use_graph, const double* f_ext, const double* phic_ext);
+
+// The solve runs on the mesh's private non-blocking stream (ordered after the caller's stream
+// with an event, and the caller's stream ordered after it), because CUDA graphs cannot be
+// captured on the legacy default stream.  When the caller's stream is itself being captured,
+// the iterations are issued directly instead (the host convergence test still synchronises,
+// so the solve as a whole cannot be part of a caller's graph).
+static fe_status poisson_solve_forked(fe_mesh* m, const double* rho, const fe_poisson_bc* bc,
+                                     double* phi, double* vbare, fe_solve_info* info,
+                                     const double* f_ext, const double* phic_ext) {
+  FE_TRY(fe_activate(m));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  FE_CUDA(cudaStreamIsCapturing(m->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return poisson_solve_on(m, rho, bc, phi, vbare, info, false, f_ext, phic_ext);
+  cudaStream_t user = m->stream;
+  FE_CUDA(cudaEventRecord(m->ev_fork, user));
+  FE_CUDA(cudaStreamWaitEvent(m->aux_stream, m->ev_fork, 0));
+  m->stream = m->aux_stream;
+  fe_status st = poisson_solve_on(m, rho, bc, phi, vbare, info, true, f_ext, phic_ext);
+  m->stream = user;
+  cudaError_t e1 = cudaEventRecord(m->ev_join, m->aux_stream);
+  cudaError_t e2 = cudaStreamWaitEvent(user, m->ev_join, 0);
+  if (st == FE_OK && (e1 != cudaSuccess || e2 != cudaSuccess)) {
+    cudaGetLastError();
+    return fe_fail(FE_ECUDA, "Poisson stream join failed");
+  }
+  return st;
+}
+
+extern "C" fe_status fe_poisson_constraints(fe_mesh* m, const fe_poisson_bc* bc,
+                                            unsigned char* mask, double* values) {
+  if (!m || !bc || !mask || !values) return fe_fail(FE_EINVAL, "fe_poisson_constraints: null argument");
+  if (!m->d_rho) return fe_fail(FE_EINVAL, "fe_poisson_constraints: call fe_set_atoms first");
+  FE_TRY(fe_activate(m));
+  const int64_t n = m->n_phi;
+  void* wsp;
+  FE_TRY(fe_ws(m, WS_CG, n * sizeof(double) * 2 + 64, &wsp));
+  double* f = (double*)wsp;
+  double* dinv = f + n;
+  k_setup<<<fe::grid_for(n), 256, 0, m->stream>>>(make_geom(m), *bc, m->d_mass, m->d_rho, m->d_b,
+                                                   m->d_vlms, nullptr, nullptr, f, dinv, mask,
+                                                   values, n); fe_count_launch();
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
+extern "C" fe_status fe_poisson_solve(fe_mesh* m, const double* rho, const fe_poisson_bc* bc,
+                                      double* phi, double* vbare, fe_solve_info* info) {
+  if (!m || !bc || !phi) return fe_fail(FE_EINVAL, "fe_poisson_solve: null argument");
+  return poisson_solve_forked(m, rho, bc, phi, vbare, info, nullptr, nullptr);
+}
+
+extern "C" fe_status fe_poisson_solve_load(fe_mesh* m, const double* f, const fe_poisson_bc* bc,
+                                           const double* phic, double* phi,
+                                           fe_solve_info* info) {
+  if (!m || !bc || !phi || !f) return fe_fail(FE_EINVAL, "fe_poisson_solve_load: null argument");
+  return poisson_solve_forked(m, nullptr, bc, phi, nullptr, info, f, phic);
+}
+
+static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisson_bc* bc,
+                                  double* phi, double* vbare, fe_solve_info* info,
+                                  bool use_graph, const double* f_ext, const double* phic_ext) {
+  if (bc->kind != FE_BIAS_CEF && bc->kind != FE_BIAS_CPD)
+    return fe_fail(FE_EINVAL, "fe_poisson_solve: bad bias kind");
+  if (!(bc->rtol > 0.0) || bc->max_iter < 1)
+    return fe_fail(FE_EINVAL, "fe_poisson_solve: need rtol > 0 and max_iter >= 1");
+  if (!m->d_rho && !(f_ext && (phic_ext || bc->kind == FE_BIAS_CEF)))
+    return fe_fail(FE_EINVAL, "fe_poisson_solve: call fe_set_atoms first");
+  if (bc->kind == FE_BIAS_CPD && !(bc->zA < bc->zB))
+    return fe_fail(FE_EINVAL, "fe_poisson_solve: need zA < zB");
+  FE_TRY(fe_activate(m));
+  const int64_t n = m->n_phi;
+  cudaStream_t st = m->stream;
+  // workspace: f, dinv, r, z, p, q (6 n doubles), mask (n bytes), partials, state
+  void* wsp;
+  size_t bytes = n * sizeof(double) * 6 + 4 * fe::RED_BLOCKS * sizeof(double) + sizeof(CgState) +
+                 n + 256;
+  FE_TRY(fe_ws(m, WS_CG, bytes, &wsp));
+  double* f = (double*)wsp;
+  double* dinv = f + n;
+  double* r = dinv + n;
+  double* z = r + n;
+  double* p = z + n;
+  double* q = p + n;
+  double* pa = q + n;
+  double* pb = pa + fe::RED_BLOCKS;
+  double* pc = pb + fe::RED_BLOCKS;
+  double* pd = pc + fe::RED_BLOCKS;
+  CgState* s = (CgState*)(pd + fe::RED_BLOCKS);
+  unsigned char* mask = (unsigned char*)(s + 1);
+  const int project = bc->kind == FE_BIAS_CEF;
+  const double* rh = rho ? rho : m->d_rho;
+  const int gb = fe::grid_for(n);
+  PGeom g = make_geom(m);
+
+  CgState s0 = {};
+  s0.maxit = bc->max_iter;
+  FE_CUDA(cudaMemcpyAsync(s, &s0, sizeof(CgState), cudaMemcpyHostToDevice, st));
+  k_setup<<<gb, 256, 0, st>>>(g, *bc, m->d_mass, rh, m->d_b, m->d_vlms, f_ext, phic_ext, f, dinv,
+                              mask, phi, n); fe_count_launch();
+  if (project) {
+    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(f, nullptr, n, pa); fe_count_launch();
+    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(m->d_mass, nullptr, n, pb); fe_count_launch();
+    k_fin_project_load<<<1, fe::RED_BLOCKS, 0, st>>>(pa, pb, s); fe_count_launch();
+    k_project_load<<<gb, 256, 0, st>>>(f, m->d_mass, s, n); fe_count_launch();
+  }
+  // r0 = f - K phi0 (phi0 = constrained values, zero elsewhere)
+  FE_TRY(fe_poisson_apply_K(m, phi, q));
+  k_resid0<<<gb, 256, 0, st>>>(f, q, mask, r, n); fe_count_launch();
+  if (project) {
+    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, nullptr, n, pa); fe_count_launch();
+    k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(pa, s, 1.0 / (double)n); fe_count_launch();
+  }
+  k_precond<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, z, dinv, mask, s, project, n, pc, pd); fe_count_launch();
+  k_fin_init<<<1, fe::RED_BLOCKS, 0, st>>>(pc, pd, s, bc->rtol); fe_count_launch();
+  k_copy<<<gb, 256, 0, st>>>(z, p, n); fe_count_launch();
+  FE_CUDA(cudaGetLastError());
+
+  // one CG iteration = 9 launches; capture a block of them into a graph
+  auto iteration = [&]() -> fe_status {
+    FE_TRY(fe_poisson_apply_K(m, p, q));
+    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(p, q, n, pa); fe_count_launch();
+    k_fin_alpha<<<1, fe::RED_BLOCKS, 0, st>>>(pa, s); fe_count_launch();
+    k_update_xr<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(phi, r, p, q, mask, s, n, pb); fe_count_launch();
+    if (project) k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(pb, s, 1.0 / (double)n); fe_count_launch();
+    k_precond<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, z, dinv, mask, s, project, n, pc, pd); fe_count_launch();
+    k_fin_beta<<<1, fe::RED_BLOCKS, 0, st>>>(pc, pd, s); fe_count_launch();
+    k_update_p<<<gb, 256, 0, st>>>(p, z, s, n); fe_count_launch();
+    return FE_OK;
+  };
+  const int per_graph = 16;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_kernels = 0;
+  if (use_graph) {
+    FE_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    fe_status cst = FE_OK;
+    const int64_t before = fe_kernel_launches();
+    for (int i = 0; i < per_graph && cst == FE_OK; ++i) cst = iteration();
+    // captured launches run only when the graph is replayed
+    graph_kernels = fe_kernel_launches() - before;
+    fe_count_launch(-graph_kernels);
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (cst != FE_OK) { cudaGetLastError(); if (graph) cudaGraphDestroy(graph); return cst; }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fe_fail(FE_ECUDA, "CG capture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphDestroy(graph);
+      return fe_fail(FE_ECUDA, "CG graph: %s", cudaGetErrorString(e));
+    }
+  }
+  CgState hs = {};
+  int launched = 0;
+  fe_status result = FE_OK;
+  while (true) {
+    FE_CUDA(cudaMemcpyAsync(&hs, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaStreamSynchronize(st));
+    if (hs.done || launched >= bc->max_iter) break;
+    if (use_graph) {
+      cudaError_t e = cudaGraphLaunch(exec, st);
+      if (e != cudaSuccess) { result = fe_fail(FE_ECUDA, "CG graph launch: %s", cudaGetErrorString(e)); break; }
+      fe_count_launch(graph_kernels);
+      launched += per_graph;
+    } else {
+      result = iteration();
+      if (result != FE_OK) break;
+      launched += 1;
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (result != FE_OK) return result;
+  if (project) {
+    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(m->d_mass, phi, n, pa); fe_count_launch();
+    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(m->d_mass, nullptr, n, pb); fe_count_launch();
+    k_shift_mean<<<gb, fe::RED_BLOCKS, 0, st>>>(phi, pa, pb, n); fe_count_launch();
+  }
+  if (vbare) {
+    k_vbare<<<fe::grid_for(m->n_psi), 256, 0, st>>>(g, phi, m->d_vlms, bc->field, project,
+                                                      m->gz_lo, vbare, m->n_psi); fe_count_launch();
+  }
+  FE_CUDA(cudaGetLastError());
+  FE_CUDA(cudaStreamSynchronize(st));
+  double rel = hs.bnorm2 > 0 ? std::sqrt(hs.rr / hs.bnorm2) : 0.0;
+  bool conv = hs.bnorm2 == 0.0 || hs.rr <= hs.tol2;
+  if (info) {
+    info->iters = hs.iters;
+    info->rel_residual = rel;
+    info->status = conv ? FE_OK : FE_ENOCONV;
+  }
+  if (!conv)
+    return fe_fail(FE_ENOCONV, "Poisson CG: %d iterations, relative residual %.3e", hs.iters, rel);
+  return FE_OK;
+}

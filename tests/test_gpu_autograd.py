@@ -1,0 +1,161 @@
+"""Differentiation form: energy parity with the oracle, adjoint Poisson gradients and the
+energy gradients (dE/d dV, dE/d field, dE/d R_z) against central finite differences
+(step 1e-4) and the Hellmann-Feynman dipole, on the 12 x 12 x 40-cell p = 4 constrained-
+potential slab (128 atoms, 370,944 phi nodes).
+
+Tolerances: gradients 1e-6 relative to central differences (the solves run to 1e-12 and the
+energy is stationary in phi, so the difference quotient carries only O(h^2) truncation and
+round-off of order 1e-14 E / h); energy vs oracle 1e-9 relative.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import assembly, poisson, potentials
+from oracle.mesh import Mesh as OMesh
+
+pytestmark = pytest.mark.gpu
+
+H_FD = 1e-4
+RTOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def fe():
+    import paper_2504_00998_gb300 as fe
+    fe.load()
+    return fe
+
+
+@pytest.fixture(scope="module")
+def ag():
+    import paper_2504_00998_gb300.autograd as ag
+    return ag
+
+
+@pytest.mark.parametrize("kind", ["cef", "cpd"])
+def test_energy_matches_oracle(fe, kind):
+    base = W.small_slab(ncell=(3, 3, 6), p=3, L=(6.0, 6.0, 16.0), natoms=3, seed=21)
+    bias = W.Bias("cef", field=0.02) if kind == "cef" else W.Bias("cpd", dV=0.04, zA=1.5, zB=14.5)
+    slab = dataclasses.replace(base, bias=bias)
+    om = OMesh(slab.L, slab.ncell, slab.p, slab.psi_dirichlet)
+    K = assembly.assemble_stiffness(om)
+    M = assembly.lumped_mass(om)
+    X = om.phi_coords()
+    rho, b = potentials.densities(X, M, slab.R, slab.Z, slab.L)
+    vl = potentials.vloc_minus_vsm(X, slab.R, slab.Z, slab.L)
+    f = 4 * math.pi * M * (rho + b)
+    if kind == "cef":
+        phi = poisson.solve_cef_direct(K, f, M)
+        vapp = potentials.v_app(X[:, 2], bias.field, slab.L[2])
+    else:
+        mask, vals, om0, om1 = potentials.cpd_constraints(X, vl, bias, slab.L)
+        phi = poisson.solve_cpd_direct(K, f, mask, vals)
+        vapp = 0 * X[:, 2]
+    E_ref = poisson.total_energy(K, phi, M, rho, b, vl, vapp)
+    m = fe.Mesh.from_slab(slab)
+    phig, _, _ = m.poisson_solve(bias, rtol=RTOL)
+    E, dEf, dEdV, *_ = m.energy(bias, phig)
+    assert abs(E - E_ref) <= 1e-9 * abs(E_ref)
+    if kind == "cpd":
+        r_ref = poisson.reaction_charge(K, phi, M, rho, b, om1)
+        assert abs(dEdV - r_ref) <= 1e-8 * max(1.0, abs(r_ref))
+    else:
+        assert abs(dEf + poisson.dipole_z(M, rho, b, X[:, 2], slab.L[2])) <= 1e-9
+
+
+@pytest.fixture(scope="module")
+def slab3():
+    return W.config3()
+
+
+def _E(fe, ag, m, slab, R, field, dV, bias):
+    return ag.slab_energy(m, R, slab.Z, bias, field=field, dV=dV, rtol=RTOL)
+
+
+def test_dE_ddV_and_dE_dR_match_finite_differences(fe, ag, slab3):
+    m = fe.Mesh.from_slab(slab3, with_atoms=False)
+    R = torch.tensor(slab3.R, dtype=torch.float64, requires_grad=True)
+    dV = torch.tensor(slab3.bias.dV, dtype=torch.float64, requires_grad=True)
+    field = torch.tensor(0.0, dtype=torch.float64)
+    E = _E(fe, ag, m, slab3, R, field, dV, slab3.bias)
+    gR, gdV = torch.autograd.grad(E, (R, dV))
+    # dE/d dV
+    Ep = _E(fe, ag, m, slab3, R.detach(), field, dV.detach() + H_FD, slab3.bias).item()
+    Em = _E(fe, ag, m, slab3, R.detach(), field, dV.detach() - H_FD, slab3.bias).item()
+    fd = (Ep - Em) / (2 * H_FD)
+    assert abs(gdV.item() - fd) <= 1e-6 * abs(fd), (gdV.item(), fd)
+    # dE/d R_z for atoms in the bottom, middle and top layers
+    scale = float(torch.max(torch.abs(gR[:, 2])))
+    for a in (0, 40, 127):
+        Rp = R.detach().clone(); Rp[a, 2] += H_FD
+        Rm = R.detach().clone(); Rm[a, 2] -= H_FD
+        fd = (_E(fe, ag, m, slab3, Rp, field, dV.detach(), slab3.bias).item() -
+              _E(fe, ag, m, slab3, Rm, field, dV.detach(), slab3.bias).item()) / (2 * H_FD)
+        g = gR[a, 2].item()
+        assert abs(g - fd) <= 1e-6 * max(abs(fd), 1e-2 * scale), (a, g, fd)
+    # an in-plane component as well
+    Rp = R.detach().clone(); Rp[5, 0] += H_FD
+    Rm = R.detach().clone(); Rm[5, 0] -= H_FD
+    fd = (_E(fe, ag, m, slab3, Rp, field, dV.detach(), slab3.bias).item() -
+          _E(fe, ag, m, slab3, Rm, field, dV.detach(), slab3.bias).item()) / (2 * H_FD)
+    assert abs(gR[5, 0].item() - fd) <= 1e-6 * max(abs(fd), 1e-2 * scale)
+
+
+def test_dE_dfield_is_minus_dipole(fe, ag, slab3):
+    """Same slab under a constant field: dE/dE = -mu_z (Section 3.1 dipole) and = FD."""
+    bias = W.Bias("cef", field=0.005)
+    m = fe.Mesh.from_slab(slab3, with_atoms=False)
+    R = torch.tensor(slab3.R, dtype=torch.float64)
+    field = torch.tensor(bias.field, dtype=torch.float64, requires_grad=True)
+    dV = torch.tensor(0.0, dtype=torch.float64)
+    E = _E(fe, ag, m, slab3, R, field, dV, bias)
+    (gf,) = torch.autograd.grad(E, (field,))
+    Ep = _E(fe, ag, m, slab3, R, field.detach() + H_FD, dV, bias).item()
+    Em = _E(fe, ag, m, slab3, R, field.detach() - H_FD, dV, bias).item()
+    fd = (Ep - Em) / (2 * H_FD)
+    assert abs(gf.item() - fd) <= 1e-6 * abs(fd)
+    rho, b, _ = m.atom_fields()
+    M = m.lumped_mass()
+    z = m.node_coords()[:, 2]
+    mu = float(torch.sum(M * (rho + b) * (z - slab3.L[2] / 2)))
+    assert abs(gf.item() + mu) <= 1e-8 * abs(mu)
+
+
+@pytest.mark.parametrize("kind", ["cef", "cpd"])
+def test_poisson_adjoint_matches_finite_differences(fe, ag, kind):
+    slab = W.small_slab(ncell=(3, 3, 6), p=3, L=(6.0, 6.0, 14.0), natoms=3, seed=9)
+    bias = W.Bias("cef", field=0.0) if kind == "cef" else W.Bias("cpd", dV=0.03, zA=1.5, zB=12.5)
+    m = fe.Mesh.from_slab(slab)
+    rng = np.random.default_rng(3)
+    n = m.n_phi
+    f0, _, _ = m.poisson_rhs()
+    w = torch.tensor(rng.standard_normal(n), device="cuda")
+    mask, vals = m.poisson_constraints(bias)
+    f = f0.clone().requires_grad_(True)
+    phic = vals.clone().requires_grad_(True) if kind == "cpd" else None
+    phi = ag.poisson_solve(m, f, bias, phic=phic, rtol=RTOL)
+    L = torch.sum(w * phi)
+    grads = torch.autograd.grad(L, (f, phic) if phic is not None else (f,))
+    d = torch.tensor(rng.standard_normal(n), device="cuda")
+    if kind == "cef":
+        d = d - d.mean()
+
+    def Lof(ff, pc):
+        return float(torch.sum(w * ag.poisson_solve(m, ff, bias, phic=pc, rtol=RTOL)))
+
+    h = 1e-3
+    fd = (Lof(f0 + h * d, phic.detach() if phic is not None else None) -
+          Lof(f0 - h * d, phic.detach() if phic is not None else None)) / (2 * h)
+    an = float(torch.sum(grads[0] * d))
+    assert abs(an - fd) <= 1e-6 * abs(fd), (an, fd)
+    if kind == "cpd":
+        dc = torch.where(mask, torch.tensor(rng.standard_normal(n), device="cuda"),
+                         torch.zeros(n, dtype=torch.float64, device="cuda"))
+        fd = (Lof(f0, phic.detach() + h * dc) - Lof(f0, phic.detach() - h * dc)) / (2 * h)
+        an = float(torch.sum(grads[1] * dc))
+        assert abs(an - fd) <= 1e-6 * abs(fd), (an, fd)

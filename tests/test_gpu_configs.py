@@ -1,0 +1,89 @@
+"""Workload-size parity: the constant-field slab end to end (12x12x36 bohr, p = 3, 32
+vectors, degree 10) against the oracle, and the p = 5 slab of 1.53 M psi nodes with 512
+vectors (the benchmark workload, same entry points and launch configuration) on sampled
+rows that the oracle evaluates one by one from the cell definition.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import assembly, chefsi, poisson, potentials
+from oracle.mesh import Mesh as OMesh
+
+pytestmark = pytest.mark.gpu
+
+R_FILTER = 0.03   # filter cut a = a0 + 0.03 (b - a0)
+
+
+@pytest.fixture(scope="module")
+def fe():
+    import paper_2504_00998_gb300 as fe
+    fe.load()
+    return fe
+
+
+def test_cef_slab_end_to_end(fe):
+    slab = W.config1()
+    om = OMesh(slab.L, slab.ncell, slab.p, slab.psi_dirichlet)
+    K = assembly.assemble_stiffness(om)
+    M = assembly.lumped_mass(om)
+    X = om.phi_coords()
+    rho, b = potentials.densities(X, M, slab.R, slab.Z, slab.L)
+    vl = potentials.vloc_minus_vsm(X, slab.R, slab.Z, slab.L)
+    phi_ref = poisson.solve_cef_direct(K, 4 * math.pi * M * (rho + b), M)
+    ids = om.psi_to_phi()
+    V = (phi_ref + vl + potentials.v_app(X[:, 2], slab.bias.field, slab.L[2]))[ids]
+    H = assembly.hamiltonian(om, V, K, M)
+
+    m = fe.Mesh.from_slab(slab)
+    phi, vbare, info = m.poisson_solve(slab.bias, rtol=1e-12)
+    assert info.status == 0
+    assert np.max(np.abs(phi.cpu().numpy() - phi_ref)) <= 1e-9 * np.max(np.abs(phi_ref))
+    assert np.max(np.abs(vbare.cpu().numpy() - V)) <= 1e-9 * np.max(np.abs(V))
+    m.set_potential(torch.tensor(V, device="cuda"))
+
+    v0 = W.lanczos_start(om.n_psi)
+    lo, hi = chefsi.lanczos_bounds(lambda v: H @ v, v0, 20)
+    glo, ghi = m.lanczos_bounds(torch.tensor(v0, device="cuda"), 20)
+    assert abs(glo - lo) <= 1e-8 * hi and abs(ghi - hi) <= 1e-8 * hi
+    a = lo + R_FILTER * (hi - lo)
+    X0 = W.start_block(slab).astype(np.float64)
+    ev_ref, _ = chefsi.chefsi_cycle(lambda Z: H @ Z, X0, slab.degree, a, hi, lo)
+    Xg = torch.tensor(X0, device="cuda")
+    m.cheb_filter(Xg, slab.degree, a, hi, lo)
+    ev = m.rayleigh_ritz(Xg).cpu().numpy()
+    assert np.max(np.abs(ev - ev_ref)) <= 1e-8
+    # the mixed (float storage, float products) path on the same cycle
+    Xf = torch.tensor(X0, dtype=torch.float32, device="cuda")
+    m.cheb_filter(Xf, slab.degree, a, hi, lo, prec=fe.FE_F32)
+    evf = m.rayleigh_ritz(Xf, prec=fe.FE_F32).cpu().numpy()
+    k = min(int(slab.n_electrons // 2), slab.nvec - 8)
+    assert np.max(np.abs(evf[:k] - ev_ref[:k])) <= 1e-5
+
+
+def test_p5_slab_sampled_rows(fe):
+    slab = W.config2()
+    om = OMesh(slab.L, slab.ncell, slab.p, slab.psi_dirichlet)
+    rng = np.random.default_rng(77)
+    V = rng.uniform(-1.5, 0.5, om.n_psi)
+    X0 = W.start_block(slab)
+    m = fe.Mesh(slab.L, slab.ncell, slab.p, slab.psi_dirichlet)
+    m.set_potential(torch.tensor(V, device="cuda"))
+    nxy = om.NX * om.NY
+    # rows on the periodic seams, the Dirichlet-adjacent planes, cell faces and interiors
+    rows = np.unique(np.concatenate([
+        [0, om.NX - 1, nxy - 1, nxy, om.n_psi - 1, om.n_psi - nxy, 5 * om.NX + 5,
+         (om.NZpsi // 2) * nxy + 3 * om.NX + 7], rng.choice(om.n_psi, 40, replace=False)]))
+    Ke = assembly.reference_cell_stiffness(om)
+    M = assembly.lumped_mass(om)
+    ref = assembly.apply_H_rows(om, V, X0, rows, Ke=Ke, M=M)
+    for prec, tol in ((fe.FE_F64, 1e-10), (fe.FE_F32, 2e-5)):
+        Xg = torch.tensor(X0, dtype=fe.storage_dtype(prec), device="cuda")
+        Y = m.apply_H(Xg, prec=prec)
+        got = Y[torch.tensor(rows, device="cuda")].double().cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol, prec
+        del Xg, Y
+        torch.cuda.empty_cache()

@@ -1,0 +1,125 @@
+"""GPU parity of the Poisson operator, load vector, atom fields and the CEF / CPD / L-CPD
+solves against the FP64 CPU oracle, plus closed forms run on the GPU.
+
+Tolerances: operator and fields <= 1e-12 relative (same arithmetic, different order);
+solves to relative residual 1e-12 on both sides, compared at 1e-9 relative (the residual
+bound times the operator's condition number on these meshes stays below that).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import assembly, poisson, potentials
+from oracle.mesh import Mesh as OMesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fe():
+    import paper_2504_00998_gb300 as fe
+    fe.load()
+    return fe
+
+
+def _oracle(slab):
+    om = OMesh(slab.L, slab.ncell, slab.p, slab.psi_dirichlet)
+    K = assembly.assemble_stiffness(om)
+    M = assembly.lumped_mass(om)
+    X = om.phi_coords()
+    return om, K, M, X
+
+
+@pytest.mark.parametrize("L,ncell,p", [((4.0, 4.0, 9.0), (2, 2, 4), 3), ((3.0, 5.0, 7.0), (3, 1, 3), 2),
+                                       ((6.0, 6.0, 6.0), (2, 2, 2), 6), ((2.0, 2.0, 4.0), (1, 1, 2), 1),
+                                       ((12.0, 12.0, 20.0), (6, 6, 10), 4)])
+def test_apply_K_matches_oracle(fe, L, ncell, p):
+    om = OMesh(L, ncell, p)
+    K = assembly.assemble_stiffness(om)
+    m = fe.Mesh(L, ncell, p)
+    x = np.random.default_rng(0).standard_normal(om.n_phi)
+    y = m.poisson_apply_K(torch.tensor(x, device="cuda")).cpu().numpy()
+    ref = K @ x
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) <= 1e-12
+    M = assembly.lumped_mass(om)
+    np.testing.assert_allclose(m.lumped_mass().cpu().numpy(), M, rtol=1e-14)
+    np.testing.assert_allclose(m.node_coords().cpu().numpy(), om.phi_coords(), atol=1e-13)
+
+
+def test_fields_and_load_match_oracle(fe):
+    slab = W.small_slab(ncell=(3, 2, 4), p=3, L=(6.0, 4.0, 12.0), natoms=4, seed=11)
+    om, K, M, X = _oracle(slab)
+    m = fe.Mesh.from_slab(slab)
+    f, rho, b = m.poisson_rhs()
+    rho_r, b_r = potentials.densities(X, M, slab.R, slab.Z, slab.L)
+    np.testing.assert_allclose(rho.cpu().numpy(), rho_r, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(b.cpu().numpy(), b_r, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(f.cpu().numpy(), 4 * math.pi * M * (rho_r + b_r), rtol=1e-11,
+                               atol=1e-14)
+
+
+@pytest.mark.parametrize("kind", ["cef", "cpd", "lcpd"])
+def test_solve_matches_oracle(fe, kind):
+    base = W.small_slab(ncell=(3, 3, 6), p=3, L=(6.0, 6.0, 14.0), natoms=3, seed=5)
+    bias = {"cef": W.Bias("cef", field=0.02),
+            "cpd": W.Bias("cpd", dV=0.03, zA=1.5, zB=12.5),
+            "lcpd": W.Bias("cpd", dV=0.03, zA=1.5, zB=12.5, patch=((1.0, 2.0), (4.0, 5.0)))}[kind]
+    slab = W.Slab(base.name, base.L, base.ncell, base.p, base.R, base.Z, bias)
+    om, K, M, X = _oracle(slab)
+    rho, b = potentials.densities(X, M, slab.R, slab.Z, slab.L)
+    vl = potentials.vloc_minus_vsm(X, slab.R, slab.Z, slab.L)
+    f = 4 * math.pi * M * (rho + b)
+    if kind == "cef":
+        ref = poisson.solve_cef_direct(K, f, M)
+        vapp = potentials.v_app(X[:, 2], bias.field, slab.L[2])
+    else:
+        mask, vals, om0, om1 = potentials.cpd_constraints(X, vl, bias, slab.L)
+        ref = poisson.solve_cpd_direct(K, f, mask, vals)
+        vapp = 0.0 * X[:, 2]
+    m = fe.Mesh.from_slab(slab)
+    phi, vbare, info = m.poisson_solve(bias, rtol=1e-12)
+    assert info.status == 0 and info.rel_residual <= 1e-12 and info.iters > 3
+    phi = phi.cpu().numpy()
+    assert np.max(np.abs(phi - ref)) <= 1e-9 * np.max(np.abs(ref))
+    ids = om.psi_to_phi()
+    vb_ref = (ref + vl + vapp)[ids]
+    assert np.max(np.abs(vbare.cpu().numpy() - vb_ref)) <= 1e-9 * np.max(np.abs(vb_ref))
+    if kind == "cef":
+        assert abs(M @ phi) <= 1e-10 * np.sum(M) * np.max(np.abs(phi))
+    else:
+        np.testing.assert_allclose((phi + vl)[om0], 0.0, atol=1e-13)
+        np.testing.assert_allclose((phi + vl)[om1], bias.dV, atol=1e-13)
+
+
+def test_patch_polynomial_and_capacitor_on_gpu(fe):
+    """No atoms: rho = -P''/(4 pi) with Dirichlet planes z = 0, Lz reproduces P exactly; with
+    rho = 0 the CPD potential is the linear capacitor profile."""
+    L, ncell, p = (3.0, 3.0, 8.0), (2, 2, 4), 4
+    om = OMesh(L, ncell, p)
+    X = om.phi_coords()
+    z = X[:, 2]
+    m = fe.Mesh(L, ncell, p)
+    m.set_atoms(np.zeros((0, 3)), np.zeros(0))
+    P = np.polynomial.Polynomial([0.0, 0.4, -0.3, 0.05, 0.01])  # degree p, P(0) = 0
+    rho = torch.tensor(-P.deriv(2)(z) / (4 * math.pi), device="cuda")
+    bias = W.Bias("cpd", dV=float(P(L[2])), zA=0.0, zB=L[2])
+    phi, _, info = m.poisson_solve(bias, rho=rho, rtol=1e-13)
+    np.testing.assert_allclose(phi.cpu().numpy(), P(z), atol=1e-10)
+    bias = W.Bias("cpd", dV=0.25, zA=2.0, zB=6.0)
+    phi, _, info = m.poisson_solve(bias, rho=torch.zeros(om.n_phi, dtype=torch.float64, device="cuda"),
+                                   rtol=1e-13)
+    np.testing.assert_allclose(phi.cpu().numpy(), np.clip((z - 2.0) / 4.0, 0, 1) * 0.25, atol=1e-11)
+
+
+def test_iteration_cap_reports_noconv(fe):
+    slab = W.small_slab(ncell=(2, 2, 4), p=3, L=(4.0, 4.0, 9.0), natoms=2)
+    m = fe.Mesh.from_slab(slab)
+    with pytest.raises(fe.FeError) as e:
+        m.poisson_solve(slab.bias, rtol=1e-14, max_iter=3)
+    assert e.value.status == fe._lib.FE_ENOCONV
+    # the mesh stays usable afterwards
+    phi, _, info = m.poisson_solve(slab.bias, rtol=1e-10)
+    assert info.status == 0
