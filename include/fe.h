@@ -117,6 +117,24 @@ fe_status fe_apply_H(fe_mesh* mesh, const void* X, void* Y, int64_t nvec, int64_
 fe_status fe_cheb_filter(fe_mesh* mesh, void* X, int64_t nvec, int64_t ld, int degree,
                          double a, double b, double a0, fe_precision prec);
 
+/* Allocation-free variant of fe_cheb_filter.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let a library call cudaMalloc -- a process whose
+ * framework allocator has already reserved the free device memory, a service that keeps a
+ * fixed memory budget after start-up, or a latency-sensitive loop where cudaMalloc's
+ * implicit device synchronisation would stall other streams.  Same arguments and result as
+ * fe_cheb_filter for FE_F64 and FE_F32 (other precisions return FE_EUNSUPPORTED); the
+ * recurrence's scratch block lives in a 64 MiB static device array compiled into the
+ * library, so n_psi * ld * sizeof(element) must not exceed 64 MiB (FE_EINVAL otherwise).
+ * The call performs no cudaMalloc / cudaFree and no allocating library call.
+ * Set-up: the first call on a device looks up the array's device address with that device
+ * current (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Sharing: every call on a device uses that device's one copy of the array, which keeps
+ * the last call's contents (the filter writes the scratch before reading it, so stale
+ * contents never matter); calls that overlap on the GPU, for example on two streams or two
+ * meshes at once, race on it. */
+fe_status fe_cheb_filter_static(fe_mesh* mesh, void* X, int64_t nvec, int64_t ld, int degree,
+                                double a, double b, double a0, fe_precision prec);
+
 typedef enum { FE_BIAS_CEF = 0, FE_BIAS_CPD = 1 } fe_bias_kind;
 
 typedef struct {

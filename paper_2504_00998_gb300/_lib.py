@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "F
 EXPORTS = [
     "fe_mesh_create", "fe_mesh_destroy", "fe_mesh_info", "fe_mesh_set_stream", "fe_node_coords",
     "fe_lumped_mass", "fe_set_atoms", "fe_set_potential", "fe_apply_H", "fe_cheb_filter",
+    "fe_cheb_filter_static",
     "fe_poisson_solve", "fe_poisson_solve_load", "fe_poisson_constraints",
     "fe_poisson_apply_K", "fe_poisson_rhs",
     "fe_rayleigh_ritz", "fe_atom_fields", "fe_energy", "fe_atom_fields_vjp",
@@ -73,6 +74,7 @@ def load(path=LIB_PATH):
         "fe_set_potential": ([P, P], I),
         "fe_apply_H": ([P, P, P, I64, I64, I], I),
         "fe_cheb_filter": ([P, P, I64, I64, I, D, D, D, I], I),
+        "fe_cheb_filter_static": ([P, P, I64, I64, I, D, D, D, I], I),
         "fe_poisson_solve": ([P, P, C.POINTER(FePoissonBC), P, P, C.POINTER(FeSolveInfo)], I),
         "fe_poisson_solve_load": ([P, P, C.POINTER(FePoissonBC), P, P, C.POINTER(FeSolveInfo)], I),
         "fe_poisson_constraints": ([P, C.POINTER(FePoissonBC), P, P], I),
