@@ -184,11 +184,15 @@ fe_status fe_poisson_apply_K(fe_mesh* mesh, const double* x_dev, double* y_dev);
 fe_status fe_poisson_rhs(fe_mesh* mesh, const double* rho_dev, double* f_dev,
                          double* rho_out_dev, double* b_out_dev);
 
-/* Orthonormalise X (Cholesky-QR, repeated; shifted Cholesky-QR3 when the first Gram is
- * ill-conditioned) and rotate it to the Ritz vectors of Ht: X <- X Q, eig_dev[nvec]
- * ascending Ritz values.  Gram matrices, the projected matrix and the rotation are
- * computed in double precision whatever the storage; float blocks are promoted to a
- * library-owned double workspace.  prec selects the arithmetic of the one Ht X product. */
+/* Rayleigh-Ritz of span(X) for Ht with orthonormal output: X <- X C with X^T X = I,
+ * X^T Ht X = diag(eig), eig_dev[nvec] ascending Ritz values (Section 2.1 orthonormality).
+ * Default: C from the Cholesky factor of the scaled Gram matrix and the projected matrix
+ * (equivalent to Cholesky-QR then Rayleigh-Ritz); when the Gram matrix is ill-conditioned
+ * the block is orthonormalised explicitly first (scaled Cholesky-QR2, shifted
+ * Cholesky-QR3 on breakdown).  Gram matrices, the projected matrix, factorisations and
+ * the rotation are in double precision whatever the storage; float blocks are promoted to
+ * a library-owned double workspace.  The one Ht X product runs in double for FE_F64 and in
+ * float (sum-factorised) for the float-storage precisions. */
 fe_status fe_rayleigh_ritz(fe_mesh* mesh, void* X, int64_t nvec, int64_t ld, double* eig_dev,
                            fe_precision prec);
 

@@ -2,16 +2,24 @@
 //
 // The Kohn-Sham problem needs the lowest N eigenpairs of H u = eps M u under the
 // orthonormality constraint <psi_i|psi_j> = delta_ij (Section 2.1).  In the symmetric form
-// used here the constraint is the Euclidean one on X.  Steps:
-//   1. S = X^T X, column scaling D = diag(S)^1/2, Cholesky of D^-1 S D^-1; if it fails the
-//      shifted Cholesky-QR3 shift s = 11 (N n + n (n+1)) u n is added (Fukaya, Kannan,
-//      Nakatsukasa, Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 2020); X <- X D^-1 R^-1.
-//   2. One more Cholesky-QR pass (Cholesky-QR2), or two after a shifted pass.
-//   3. Hs = X^T (Ht X), symmetrised; Hs = Q diag(eps) Q^T (dense symmetric eigensolver);
-//      X <- X Q.
-// The wavefunction block is node-major with the vectors contiguous; in column-major BLAS
-// terms it is A = X^T (nvec x N, lda = ld).  Gram matrices and products are plain cuBLAS
-// double GEMMs, the n x n factorisations are cuSOLVER calls.
+// used here the constraint is the Euclidean one on X.
+//
+// Default (Gram) path, five N n^2 double flops instead of thirteen:
+//   S = X^T X (SYRK), Hs = X^T (Ht X) (GEMM), D = diag(S)^-1/2,
+//   D S D = R^T R (Cholesky), G = R^-T D Hs D R^-1, G = Q diag(eps) Q^T,
+//   X <- X C with C = D R^-1 Q (GEMM).
+// X C is the Rayleigh-Ritz basis of span(X) with C^T S C = I: the same result as
+// Cholesky-QR followed by Rayleigh-Ritz, with the orthonormalisation folded into the n x n
+// problem.  Its orthogonality degrades like cond(D S D) u, so when the Cholesky fails or
+// the factor's diagonal indicates cond(D S D) > 1e8 (cold starts from random blocks) the
+// explicit path runs instead:
+//   scaled Cholesky-QR2, or shifted Cholesky-QR3 when the first factorisation breaks down
+//   (shift 11 (N n + n (n+1)) u n; Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa, SIAM
+//   J. Sci. Comput. 2020), then Hs = X^T (Ht X), eigh, X <- X Q.
+// The block is node-major with the vectors contiguous; in column-major BLAS terms it is
+// A = X^T (nvec x N, lda = ld).  The big products are plain cuBLAS double GEMM / SYRK
+// calls, the n x n factorisations cuSOLVER calls.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -20,6 +28,9 @@
 
 fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t nvec, int64_t ld,
                      double alpha, double beta, double shift, fe_precision prec);
+
+// the lower triangle of a SYRK result (upper stored) is filled in (defined below)
+__global__ void k_fill_lower(double* __restrict__ S, int n);
 
 namespace {
 
@@ -96,7 +107,10 @@ fe_status gram(fe_mesh* m, const double* A, int64_t lda, const double* B, int64_
 fe_status cholqr_pass(fe_mesh* m, double* X, int64_t ld, int64_t nvec, RrWs& w, double shift,
                       int* broke) {
   const int n = (int)nvec;
-  FE_TRY(gram(m, X, ld, X, ld, nvec, w.S));
+  const double one_ = 1.0, zero_ = 0.0;
+  FE_CUBLAS(cublasDsyrk(m->cublas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, n, (int)m->n_psi, &one_,
+                        X, (int)ld, &zero_, w.S, n));
+  k_fill_lower<<<fe::grid_for((int64_t)n * n), 256, 0, m->stream>>>(w.S, n); fe_count_launch();
   k_scale_gram<<<1, 256, 0, m->stream>>>(w.S, n, w.d, shift); fe_count_launch();
   k_scale_cols<<<fe::grid_for(m->n_psi * nvec), 256, 0, m->stream>>>(X, ld, nvec, m->n_psi, w.d); fe_count_launch();
   FE_CUSOLVER(cusolverDnDpotrf(m->cusolver, CUBLAS_FILL_MODE_UPPER, n, w.S, n, w.work, w.lwork,
@@ -115,15 +129,98 @@ fe_status cholqr_pass(fe_mesh* m, double* X, int64_t ld, int64_t nvec, RrWs& w, 
 
 }  // namespace
 
-// Orthonormalise and Rayleigh-Ritz the double block X64 [n_psi][ld64] in place.
-fe_status fe_rr_f64(fe_mesh* m, double* X, int64_t nvec, int64_t ld, double* eig) {
+__global__ void k_scale_sym(double* __restrict__ A, int n, const double* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(i % n), c = (int)(i / n);
+    A[i] *= d[r] * d[c];
+  }
+}
+
+// d[j] = 1 / sqrt(S_jj) (diagonal scaling of the Gram matrix)
+__global__ void k_inv_sqrt_diag(const double* __restrict__ S, int n, double* __restrict__ d) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    d[j] = 1.0 / sqrt(S[(int64_t)j * n + j]);
+}
+
+__global__ void k_fill_lower(double* __restrict__ S, int n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(i % n), c = (int)(i / n);
+    if (r > c) S[i] = S[(int64_t)r * n + c];
+  }
+}
+
+__global__ void k_scale_rows(double* __restrict__ C, int n, const double* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    C[i] *= d[(int)(i % n)];
+}
+
+__global__ void k_diag(const double* __restrict__ R, int n, double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    out[j] = R[(int64_t)j * n + j];
+}
+
+// Gram path.  HX is the block Ht X (double, same layout).  X is overwritten by X C into Xout
+// (may equal X only through the temporary tmp).  *ill = true when the caller must fall
+// back to the explicit orthonormalisation.
+fe_status rr_gram_path(fe_mesh* m, const double* X, int64_t ld, const double* HX, int64_t ldh,
+                       int64_t nvec, RrWs& w, double* Xout, int64_t ldo, double* eig, bool* ill) {
   const int n = (int)nvec;
   cudaStream_t st = m->stream;
-  // small workspace
+  const double one = 1.0, zero = 0.0;
+  *ill = false;
+  // S = A A^T (upper), Hs = A B^T
+  FE_CUBLAS(cublasDsyrk(m->cublas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, n, (int)m->n_psi, &one,
+                        X, (int)ld, &zero, w.S, n));
+  FE_TRY(gram(m, X, ld, HX, ldh, nvec, w.Q));
+  k_inv_sqrt_diag<<<(n + 255) / 256, 256, 0, st>>>(w.S, n, w.d); fe_count_launch();
+  k_fill_lower<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.S, n); fe_count_launch();
+  k_scale_sym<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.S, n, w.d); fe_count_launch();
+  k_symmetrize<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.Q, n); fe_count_launch();
+  k_scale_sym<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.Q, n, w.d); fe_count_launch();
+  FE_CUSOLVER(cusolverDnDpotrf(m->cusolver, CUBLAS_FILL_MODE_UPPER, n, w.S, n, w.work, w.lwork,
+                               w.info));
+  k_diag<<<(n + 255) / 256, 256, 0, st>>>(w.S, n, w.eig); fe_count_launch();
+  std::vector<double> rdiag(n);
+  int hinfo = 0;
+  FE_CUDA(cudaMemcpyAsync(&hinfo, w.info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FE_CUDA(cudaMemcpyAsync(rdiag.data(), w.eig, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  FE_CUDA(cudaStreamSynchronize(st));
+  if (hinfo != 0) { *ill = true; return FE_OK; }
+  double rmax = 0.0, rmin = 1e300;
+  for (int j = 0; j < n; ++j) {
+    rmax = std::fmax(rmax, std::fabs(rdiag[j]));
+    rmin = std::fmin(rmin, std::fabs(rdiag[j]));
+  }
+  if (!(rmin > 0.0) || (rmax / rmin) * (rmax / rmin) > 1e8) { *ill = true; return FE_OK; }
+  // G = R^-T Hs R^-1
+  FE_CUBLAS(cublasDtrsm(m->cublas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T,
+                        CUBLAS_DIAG_NON_UNIT, n, n, &one, w.S, n, w.Q, n));
+  FE_CUBLAS(cublasDtrsm(m->cublas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                        CUBLAS_DIAG_NON_UNIT, n, n, &one, w.S, n, w.Q, n));
+  k_symmetrize<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.Q, n); fe_count_launch();
+  FE_CUSOLVER(cusolverDnDsyevd(m->cusolver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n,
+                               w.Q, n, w.eig, w.work, w.lwork, w.info));
+  // C = D R^-1 Q
+  FE_CUBLAS(cublasDtrsm(m->cublas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                        CUBLAS_DIAG_NON_UNIT, n, n, &one, w.S, n, w.Q, n));
+  k_scale_rows<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.Q, n, w.d); fe_count_launch();
+  // Xout^T = C^T A
+  FE_CUBLAS(cublasDgemm(m->cublas, CUBLAS_OP_T, CUBLAS_OP_N, n, (int)m->n_psi, n, &one, w.Q, n,
+                        X, (int)ld, &zero, Xout, (int)ldo));
+  FE_CUDA(cudaMemcpyAsync(eig, w.eig, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  FE_CUDA(cudaMemcpyAsync(&hinfo, w.info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FE_CUDA(cudaStreamSynchronize(st));
+  if (hinfo != 0) return fe_fail(FE_ECUDA, "syevd info %d", hinfo);
+  return FE_OK;
+}
+
+fe_status rr_setup_small(fe_mesh* m, int n, RrWs& w) {
   int lw_potrf = 0, lw_syevd = 0;
   void* wsp;
   FE_TRY(fe_ws(m, WS_RR_SMALL, sizeof(double) * ((size_t)2 * n * n + 2 * n) + 64, &wsp));
-  RrWs w;
   w.S = (double*)wsp;
   w.Q = w.S + (size_t)n * n;
   w.d = w.Q + (size_t)n * n;
@@ -136,6 +233,16 @@ fe_status fe_rr_f64(fe_mesh* m, double* X, int64_t nvec, int64_t ld, double* eig
   FE_TRY(fe_ws(m, WS_TC, sizeof(double) * ((size_t)w.lwork + 8), &wk));
   w.work = (double*)wk;
   w.info = (int*)(w.work + w.lwork);
+  return FE_OK;
+}
+
+// Orthonormalise and Rayleigh-Ritz the double block X64 [n_psi][ld64] in place (explicit
+// path: Cholesky-QR2 or shifted Cholesky-QR3, then Rayleigh-Ritz with an FP64 Ht X).
+fe_status fe_rr_f64(fe_mesh* m, double* X, int64_t nvec, int64_t ld, double* eig) {
+  const int n = (int)nvec;
+  cudaStream_t st = m->stream;
+  RrWs w;
+  FE_TRY(rr_setup_small(m, n, w));
 
   // Cholesky-QR2, or shifted Cholesky-QR3 when the first factorisation breaks down
   int broke = 0;
@@ -180,22 +287,54 @@ extern "C" fe_status fe_rayleigh_ritz(fe_mesh* m, void* X, int64_t nvec, int64_t
   if (nvec < 1 || ld < nvec || nvec > 16384)
     return fe_fail(FE_EINVAL, "fe_rayleigh_ritz: need 1 <= nvec <= ld, nvec <= 16384");
   if (nvec > m->n_psi) return fe_fail(FE_EINVAL, "fe_rayleigh_ritz: nvec exceeds the node count");
-  int eb = prec == FE_F64 ? 8 : 4;
+  if (prec != FE_F64 && prec != FE_F32 && prec != FE_BF16_F32ACC && prec != FE_F32_F32ACC)
+    return fe_fail(FE_EINVAL, "fe_rayleigh_ritz: bad precision");
+  const int eb = prec == FE_F64 ? 8 : 4;
   if (((uintptr_t)X) % 16 || (ld * eb) % 16)
     return fe_fail(FE_EINVAL, "fe_rayleigh_ritz: block alignment");
   if (!m->has_potential) return fe_fail(FE_EINVAL, "fe_rayleigh_ritz: call fe_set_potential first");
   FE_TRY(fe_activate(m));
-  if (prec == FE_F64) return fe_rr_f64(m, (double*)X, nvec, ld, eig);
-  // float storage: promote to a double workspace, work there, demote
-  int64_t ld64 = (nvec + 1) / 2 * 2;
+  const int n = (int)nvec;
+  const int64_t N = m->n_psi;
+  RrWs w;
+  FE_TRY(rr_setup_small(m, n, w));
+  const int gb = fe::grid_for(N * nvec);
+  const int64_t ld64 = (nvec + 1) / 2 * 2;
+  void* hxp;
+  FE_TRY(fe_ws(m, WS_RR_HX, sizeof(double) * (size_t)N * (prec == FE_F64 ? ld : ld64), &hxp));
+  double* HX = (double*)hxp;
+  bool ill = false;
+  if (prec == FE_F64) {
+    double* Xd = (double*)X;
+    FE_TRY(fe_hx_step(m, Xd, HX, nullptr, nvec, ld, 1.0, 0.0, 0.0, FE_F64));
+    void* tp;
+    FE_TRY(fe_ws(m, WS_RR_X, sizeof(double) * (size_t)N * ld, &tp));
+    FE_TRY(rr_gram_path(m, Xd, ld, HX, ld, nvec, w, (double*)tp, ld, eig, &ill));
+    if (!ill) {
+      FE_CUDA(cudaMemcpy2DAsync(Xd, ld * 8, tp, ld * 8, nvec * 8, N, cudaMemcpyDeviceToDevice,
+                                m->stream));
+      return FE_OK;
+    }
+    return fe_rr_f64(m, Xd, nvec, ld, eig);
+  }
+  // float storage: Ht X in float (sum-factorised), Gram, projection and rotation in double
   void* xp;
-  FE_TRY(fe_ws(m, WS_RR_X, sizeof(double) * (size_t)m->n_psi * ld64, &xp));
+  const size_t half = sizeof(double) * (size_t)N * ld64;
+  const size_t second = std::max(half, sizeof(float) * (size_t)N * ld);
+  FE_TRY(fe_ws(m, WS_RR_X, half + second, &xp));
   double* X64 = (double*)xp;
-  const int gb = fe::grid_for(m->n_psi * nvec);
-  k_f2d<<<gb, 256, 0, m->stream>>>((const float*)X, ld, X64, ld64, nvec, m->n_psi); fe_count_launch();
+  double* T64 = X64 + (size_t)N * ld64;
+  float* HXf = (float*)T64;   // float Ht X staged in the second half before promotion
+  FE_TRY(fe_hx_step(m, X, HXf, nullptr, nvec, ld, 1.0, 0.0, 0.0, FE_F32));
+  k_f2d<<<gb, 256, 0, m->stream>>>(HXf, ld, HX, ld64, nvec, N); fe_count_launch();
+  k_f2d<<<gb, 256, 0, m->stream>>>((const float*)X, ld, X64, ld64, nvec, N); fe_count_launch();
   FE_CUDA(cudaGetLastError());
-  FE_TRY(fe_rr_f64(m, X64, nvec, ld64, eig));
-  k_d2f2<<<gb, 256, 0, m->stream>>>(X64, ld64, (float*)X, ld, nvec, m->n_psi); fe_count_launch();
+  FE_TRY(rr_gram_path(m, X64, ld64, HX, ld64, nvec, w, T64, ld64, eig, &ill));
+  if (ill) {
+    FE_TRY(fe_rr_f64(m, X64, nvec, ld64, eig));
+    T64 = X64;
+  }
+  k_d2f2<<<gb, 256, 0, m->stream>>>(T64, ld64, (float*)X, ld, nvec, N); fe_count_launch();
   FE_CUDA(cudaGetLastError());
   return FE_OK;
 }

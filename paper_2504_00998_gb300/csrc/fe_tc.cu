@@ -3,9 +3,9 @@
 // Section 2.3 FE discretization: the stiffness K = sum_e P_e^T K_e P_e with the exactly
 // integrated cell matrix K_e (dense (p+1)^3 x (p+1)^3; identical for every cell of the
 // uniform mesh).  Here the Hamiltonian part 1/2 M^-1/2 K M^-1/2 X is evaluated as
-//   kernel 1 (tensor cores): for every cell e and 64-vector tile, y_e = (1/2 K_e) (S X)_e
+//   kernel 1 (tensor cores): for every cell e and 64-vector tile, y_e = K_e (S X)_e
 //     with S = M^-1/2, as a 128-row (M) x 224 (K) x 64 (N) bf16 product per M tile on
-//     tcgen05 with fp32 accumulation in tensor memory.  1/2 K_e lives in shared memory for
+//     tcgen05 with fp32 accumulation in tensor memory.  K_e lives in shared memory for
 //     the whole persistent CTA (one cp.async.bulk copy of a pre-swizzled image); the cell
 //     tile is gathered from the node-major block, scaled by S, rounded to bf16 and written
 //     in the UMMA K-major 128-byte-swizzle layout; two stages alternate so the gather of
@@ -51,7 +51,7 @@ struct TcShape {
 struct TcArgs {
   const float* X; int64_t ldx; int64_t nvec;
   float* Ycell;                 // [nvt][ncells][NE][64]
-  const unsigned char* Aimg;    // pre-swizzled 1/2 K_e image, A_BYTES
+  const unsigned char* Aimg;    // pre-swizzled K_e image, A_BYTES
   int* err;
   int nx, ny, nz, NX, NY, gz_lo, NZs, nvt;
   int64_t ncells;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_cells_kernel(const TcArgs a)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // the constant 1/2 K_e image: one bulk copy, consumed only by the tensor core, so only the
+  // the constant K_e image: one bulk copy, consumed only by the tensor core, so only the
   // issuing thread waits for it
   if (tid == 0) {
     mbar_expect_tx(smem_u32(&mbar[2]), (uint32_t)S::A_BYTES);
@@ -411,7 +411,8 @@ __global__ void tc_assemble_kernel(const AsmArgs a) {
   }
 }
 
-// host image of 1/2 K_e in the kernel's swizzled K-major layout (rows = output local node)
+// host image of K_e in the kernel's swizzled K-major layout (rows = output local node); the
+// factor 1/2 of the kinetic term is applied with the output scale in the assembly kernel
 template <int P>
 std::vector<unsigned char> build_image(const fe_mesh* m) {
   using S = TcShape<P>;
@@ -426,7 +427,7 @@ std::vector<unsigned char> build_image(const fe_mesh* m) {
       double v = ax * m->K1[i][i2] * m->M1[j][j2] * m->M1[k][k2] +
                  ay * m->M1[i][i2] * m->K1[j][j2] * m->M1[k][k2] +
                  az * m->M1[i][i2] * m->M1[j][j2] * m->K1[k][k2];
-      __nv_bfloat16 b = __float2bfloat16_rn((float)(0.5 * v));
+      __nv_bfloat16 b = __float2bfloat16_rn((float)v);
       const int mt = I / 128, row = I % 128;
       const int chunk = Jn / 8, within = Jn % 8;
       const int atom = chunk / 8, cc = chunk % 8;
