@@ -42,7 +42,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--prec", choices=["f32", "f64", "bf16", "f32x3"], default="f32")
-    ap.add_argument("--workload", choices=["p5", "p5s", "p3"], default="p5")
+    ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep"], default="p5",
+                    help="p5: the benchmark slab; p5s / p3: smaller slabs; sweep: the batched "
+                         "bias sweep of 24 independent 8x8xH-cell p=4 slabs")
+    ap.add_argument("--rr", choices=["f64", "tc32"], default="tc32",
+                    help="Rayleigh-Ritz block products for float storage: double GEMMs or "
+                         "FP32-accurate tensor-core emulation (n x n part always double)")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -167,6 +172,45 @@ def gpu_index(dev):
     return dev.index if dev.index is not None else torch.cuda.current_device()
 
 
+def reduce_over_ranks(dist, device, elapsed_ms, launches):
+    """Replicas: the job's time is the slowest rank's, its kernel launches the sum over
+    ranks (identity without a process group)."""
+    if dist is None:
+        return elapsed_ms, launches
+    import torch
+    t = torch.tensor([float(elapsed_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([int(launches)], device=device, dtype=torch.int64)
+    dist.all_reduce(n)
+    return float(t.item()), int(n.item())
+
+
+def aggregate_value(world, flops_per_rank_step, ms_step):
+    """Whole-job throughput: the work of all ranks over the slowest rank's step time."""
+    return world * flops_per_rank_step / (ms_step * 1e-3) / 1e12
+
+
+def _host_threads():
+    return max(1, os.cpu_count() or 1)
+
+
+def oracle_hx_threaded(H, X, threads):
+    """The oracle's CSR product H X, its vector columns split into one contiguous block per
+    host thread (scipy's sparse kernel releases the GIL, so the blocks run in parallel)."""
+    from concurrent.futures import ThreadPoolExecutor
+    nvec = X.shape[1]
+    edges = np.linspace(0, nvec, threads + 1).astype(int)
+    blocks = [(edges[i], edges[i + 1]) for i in range(threads) if edges[i + 1] > edges[i]]
+    Y = np.empty((H.shape[0], nvec))
+
+    def one(b):
+        Y[:, b[0]:b[1]] = H @ np.ascontiguousarray(X[:, b[0]:b[1]])
+
+    with ThreadPoolExecutor(len(blocks)) as ex:
+        list(ex.map(one, blocks))
+    return Y, len(blocks)
+
+
 def cpu_baseline_oracle(slab, nvec, seed=5):
     """Oracle CSR H X on a 2-cell-thick slice of the same slab (bounded CPU sample)."""
     from oracle import assembly
@@ -177,16 +221,17 @@ def cpu_baseline_oracle(slab, nvec, seed=5):
     rng = np.random.default_rng(seed)
     H = assembly.hamiltonian(om, rng.uniform(-1, 0.5, om.n_psi))
     X = rng.standard_normal((om.n_psi, nvec))
-    H @ X[:, :8]
+    threads = _host_threads()
+    oracle_hx_threaded(H, X[:, :2 * threads], threads)
     t0 = time.perf_counter()
-    H @ X
+    _, used = oracle_hx_threaded(H, X, threads)
     dt = time.perf_counter() - t0
     ne = (slab.p + 1) ** 3
     flops = 2.0 * ne * ne * om.n_cells * nvec
-    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": used, "kind": "oracle",
             "sample": (f"oracle scipy CSR Ht X, one application, {nc[0]}x{nc[1]}x{nc[2]} cells "
                        f"slice of the slab (p={slab.p}, {om.n_psi:,} psi nodes x {nvec} "
-                       f"vectors), single-threaded sparse kernel, {dt:.2f} s"),
+                       f"vectors), vector columns split over {used} host threads, {dt:.2f} s"),
             "seconds": dt}
 
 
@@ -208,22 +253,25 @@ def run_reference(args):
     X = rng.standard_normal((om.n_psi, nvec))
     ne = (slab.p + 1) ** 3
     flops = 2.0 * ne * ne * om.n_cells * nvec
+    threads = _host_threads()
     for _ in range(args.warmup):
-        H @ X
+        oracle_hx_threaded(H, X, threads)
     t0 = time.perf_counter()
+    used = threads
     for _ in range(args.steps):
-        H @ X
+        _, used = oracle_hx_threaded(H, X, threads)
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
     val = flops / dt / 1e12
     sample = (f"one oracle scipy CSR Ht X per step on a {nc[0]}x{nc[1]}x{nc[2]}-cell slice of "
-              f"the slab (p={slab.p}, {om.n_psi:,} psi nodes x {nvec} vectors)")
+              f"the slab (p={slab.p}, {om.n_psi:,} psi nodes x {nvec} vectors), vector "
+              f"columns split over {used} host threads")
     line = {
         "impl": "reference", "metric": "Cheb-filter H·X nominal TFLOP/s", "value": val,
         "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_desc(slab), "sample": sample},
-        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": used, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -254,6 +302,8 @@ def run_gpu(args):
     lib = fe.load()
 
     m = fe.Mesh.from_slab(slab, device=local)
+    if prec != fe.FE_F64:
+        m.set_rr_products(args.rr == "tc32")
     phi = torch.empty(m.n_phi, dtype=torch.float64, device=dev)
     vb = torch.empty(m.n_psi, dtype=torch.float64, device=dev)
     m.poisson_solve(slab.bias, rtol=POISSON_RTOL, phi=phi, vbare=vb)
@@ -305,13 +355,8 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
     launches = lib.fe_kernel_launches() - n0
     elapsed_ms = t_start.elapsed_time(t_end)
+    elapsed_ms, launches = reduce_over_ranks(dist, dev, elapsed_ms, launches)
     if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-        lt = torch.tensor([launches], device=dev, dtype=torch.int64)
-        dist.all_reduce(lt)
-        launches = int(lt.item())
         dist.barrier()
     phase = np.zeros(4)
     for e in marks:
@@ -321,7 +366,7 @@ def run_gpu(args):
     ms_step = elapsed_ms / args.steps
     flops_hx = nominal_flops_per_hx(slab, nvec)
     flops_step = flops_hx * (degree + 1)
-    value = world * flops_step / (ms_step * 1e-3) / 1e12
+    value = aggregate_value(world, flops_step, ms_step)
 
     # roofline of the dominant kernel: the fused Chebyshev operator launch
     eb = 8 if prec == fe.FE_F64 else 4
@@ -349,27 +394,29 @@ def run_gpu(args):
     e2e_end.record(st)
     torch.cuda.synchronize(dev)
     e2e_ms = e2e_start.elapsed_time(e2e_end) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = world * flops_step / (e2e_ms * 1e-3) / 1e12
+    e2e_ms, _ = reduce_over_ranks(dist, dev, e2e_ms, 0)
+    e2e_val = aggregate_value(world, flops_step, e2e_ms)
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_fp64_compare and prec != fe.FE_F64:
         # one cycle of both paths from the same start block: Ritz-value difference and the
         # FP64 filter's throughput
+        # two cycles (the second starts from an orthonormal block, as in an SCF loop)
         Xm = torch.empty((n, nvec), dtype=fe.storage_dtype(prec), device=dev)
         Xm.copy_(X0.to(Xm.dtype))
-        m.cheb_filter(Xm, degree, a, b, a0, prec=prec)
-        ev_m = m.rayleigh_ritz(Xm, prec=prec).cpu().numpy()
+        for _ in range(2):
+            m.cheb_filter(Xm, degree, a, b, a0, prec=prec)
+            ev_m = m.rayleigh_ritz(Xm, prec=prec).cpu().numpy()
         del Xm
         Xd = X0.to(dev).double()
         f0, f1 = ev(), ev()
-        f0.record(st)
-        m.cheb_filter(Xd, degree, a, b, a0, prec=fe.FE_F64)
-        f1.record(st)
-        ev_d = m.rayleigh_ritz(Xd, prec=fe.FE_F64).cpu().numpy()
+        for cyc in range(2):
+            if cyc == 1:
+                f0.record(st)
+            m.cheb_filter(Xd, degree, a, b, a0, prec=fe.FE_F64)
+            if cyc == 1:
+                f1.record(st)
+            ev_d = m.rayleigh_ritz(Xd, prec=fe.FE_F64).cpu().numpy()
         torch.cuda.synchronize(dev)
         fms = f0.elapsed_time(f1)
         del Xd
@@ -394,6 +441,7 @@ def run_gpu(args):
             "config": {"workload": workload_desc(slab),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (block of %.1f GB)" % (n * nvec * eb / 1e9),
+                       "rr_products": args.rr if prec != fe.FE_F64 else "f64",
                        "filter_bounds": {"a0": a0, "a": a, "b": b}},
             "phases_ms": {"poisson_and_veff": phase[0], "set_potential": phase[1],
                           "cheb_filter": phase[2], "cholqr_rr": phase[3]},
@@ -419,10 +467,111 @@ def run_gpu(args):
     return 0
 
 
+def run_sweep(args):
+    """Batched bias sweep: 24 independent slabs of 8 x 8 x H cells (p = 4, 128 vectors),
+    half under a constant field and half under a constrained potential difference, stepped
+    together.  One step = the degree-20 Chebyshev filter of every slab as batched launches
+    (one kernel per filter step over all instances) and the Cholesky-QR / Rayleigh-Ritz of
+    each slab.  The Poisson solves that give each slab's V_eff run once before timing."""
+    import torch
+    import paper_2504_00998_gb300 as fe
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    lib = fe.load()
+    slabs = W.config4()
+    meshes, Xs, bounds = [], [], []
+    for sl in slabs:
+        m = fe.Mesh.from_slab(sl)
+        m.set_rr_products(args.rr == "tc32")
+        _, vb, _ = m.poisson_solve(sl.bias, rtol=POISSON_RTOL)
+        m.set_potential(vb)
+        lo, hi = m.lanczos_bounds(torch.tensor(W.lanczos_start(m.n_psi), device=dev),
+                                  LANCZOS_STEPS)
+        bounds.append((lo + R_FILTER * (hi - lo), hi, lo))
+        meshes.append(m)
+        Xs.append(torch.from_numpy(W.start_block(sl)).to(dev))
+    batch = fe.Batch(meshes)
+    degree = slabs[0].degree
+    a = [t[0] for t in bounds]
+    b = [t[1] for t in bounds]
+    a0 = [t[2] for t in bounds]
+    st = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    fl, rr = [], []
+
+    def step(rec):
+        e = [ev() for _ in range(3)]
+        e[0].record(st)
+        batch.cheb_filter(Xs, degree, a, b, a0, prec=fe.FE_F32)
+        e[1].record(st)
+        for mm, X in zip(meshes, Xs):
+            mm.rayleigh_ritz(X, prec=fe.FE_F32)
+        e[2].record(st)
+        if rec:
+            fl.append((e[0], e[1]))
+            rr.append((e[1], e[2]))
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize(dev)
+    n0 = lib.fe_kernel_launches()
+    t0, t1 = ev(), ev()
+    with ClockSampler(gpu_index(dev)) as clk:
+        t0.record(st)
+        for _ in range(args.steps):
+            step(True)
+        t1.record(st)
+        torch.cuda.synchronize(dev)
+    launches = lib.fe_kernel_launches() - n0
+    ms_step = t0.elapsed_time(t1) / args.steps
+    f_ms = sum(x.elapsed_time(y) for x, y in fl) / len(fl)
+    r_ms = sum(x.elapsed_time(y) for x, y in rr) / len(rr)
+    nvec = slabs[0].nvec
+    flops_hx = sum(nominal_flops_per_hx(sl, nvec) for sl in slabs)
+    value = flops_hx * (degree + 1) / (ms_step * 1e-3) / 1e12
+    n_all = sum(mm.n_psi for mm in meshes)
+    bytes_filter = (2 + 3 * (degree - 1)) * n_all * nvec * 4 + degree * n_all * 4
+    achieved = bytes_filter / degree / (f_ms / degree * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    heights = [sl.ncell[2] for sl in slabs]
+    line = {
+        "metric": "Cheb-filter H·X nominal TFLOP/s", "value": value, "unit": "TFLOP/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": (f"bias sweep: {len(slabs)} slabs of 8x8xH cells, H from "
+                                f"{min(heights)} to {max(heights)}, p=4, {n_all:,} psi nodes "
+                                f"in all, {nvec} vectors each, Chebyshev degree {degree}, "
+                                "12 CEF + 12 CPD"),
+                   "parallelism": "single GPU, one batched launch per filter step",
+                   "l2": "inputs larger than L2 (blocks of %.1f GB in all)" % (n_all * nvec * 4 / 1e9),
+                   "rr_products": args.rr},
+        "phases_ms": {"batched_cheb_filter": f_ms, "cholqr_rr_all": r_ms},
+        "filter_tflops": flops_hx * degree / (f_ms * 1e-3) / 1e12,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                     "kernel": "kron_batch_f32_p4",
+                     "algorithmic_bytes_per_launch": bytes_filter / degree,
+                     "launch_ms": f_ms / degree},
+        "cpu_baseline": None,
+        "e2e": None,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    batch.close()
+    for mm in meshes:
+        mm.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_gpu(args)
 
 

@@ -87,6 +87,26 @@ fe_status fe_mesh_info(const fe_mesh* mesh, int64_t* n_phi, int64_t* n_psi, int6
 /* Replace the stream used by all later calls on this mesh. */
 fe_status fe_mesh_set_stream(fe_mesh* mesh, void* stream);
 
+/* Per-mesh options.
+ *   FE_OPT_RR_PRODUCTS: arithmetic of the three block products of fe_rayleigh_ritz for
+ *     float-storage blocks.  FE_RR_PRODUCTS_F64 (default): double GEMMs on a promoted copy.
+ *     FE_RR_PRODUCTS_TC32: X^T X, X^T (Ht X) and X C as tensor-core GEMMs in cuBLAS's
+ *     FP32-accurate BF16x9 emulation on the float block (relative error ~1e-7, the
+ *     precision of the float storage itself); the n x n Cholesky, projection and
+ *     eigensolve stay in double.  FE_F64 blocks always use double GEMMs. */
+enum { FE_OPT_RR_PRODUCTS = 0, FE_OPT_POISSON_PRECOND = 1 };
+enum { FE_RR_PRODUCTS_F64 = 0, FE_RR_PRODUCTS_TC32 = 1 };
+/*   FE_OPT_POISSON_PRECOND: preconditioner of the Poisson CG.  FE_PRECOND_JACOBI: the
+ *     diagonal of K.  FE_PRECOND_JACOBI_PLANES (default): the diagonal plus an exact solve
+ *     on the coarse space of z-planes (one basis function per phi plane: the indicator of
+ *     its free nodes), i.e. M^-1 = D^-1 + R^T (R K R^T)^-1 R with R the free-node plane
+ *     sums.  The coarse matrix is banded (planes within one cell layer couple) and is
+ *     factorised once per solve.  It removes the slow modes that are constant over x and y,
+ *     which dominate on long slabs.  The converged solution is the same; only the
+ *     iteration count changes. */
+enum { FE_PRECOND_JACOBI = 0, FE_PRECOND_JACOBI_PLANES = 1 };
+fe_status fe_set_option(fe_mesh* mesh, int option, int64_t value);
+
 /* Node coordinates in phi order, xyz_dev[n_phi][3] (Section 2.3 node layout). */
 fe_status fe_node_coords(const fe_mesh* mesh, double* xyz_dev);
 /* Diagonal of the GLL-lumped overlap M on phi nodes, m_dev[n_phi]. */
@@ -134,6 +154,33 @@ fe_status fe_cheb_filter(fe_mesh* mesh, void* X, int64_t nvec, int64_t ld, int d
  * meshes at once, race on it. */
 fe_status fe_cheb_filter_static(fe_mesh* mesh, void* X, int64_t nvec, int64_t ld, int degree,
                                 double a, double b, double a0, fe_precision prec);
+
+/* ---- batches of independent slabs -------------------------------------------------------
+ * A bias sweep (Section 3: one slab under a series of fields or potential differences, or
+ * slabs of several thicknesses) is a set of independent eigenproblems.  A batch applies
+ * each operator step to all of them in ONE kernel launch: Ht_i X_i for every instance i,
+ * with the instance's own geometry, potential and block.  Instances must share p and the
+ * cell size h (one element coefficient table); their cell counts, psi z-face conditions and
+ * potentials may differ.  All meshes must be on one device and one stream; batched calls
+ * run on that stream.  The batch borrows the meshes (destroy it before them) and owns only
+ * a small device array of per-instance descriptors.  Only FE_F64 and FE_F32 are batched
+ * (FE_EUNSUPPORTED otherwise).  A different p or cell size returns FE_EUNSUPPORTED. */
+typedef struct fe_batch fe_batch;
+fe_status fe_batch_create(fe_mesh* const* meshes, int n, fe_batch** out);
+fe_status fe_batch_destroy(fe_batch* batch);
+
+/* Y_i = Ht_i X_i for every instance (fe_apply_H per instance, one launch).  X, Y: host
+ * arrays of n device pointers; nvec, ld: host arrays of n counts; same layout and alignment
+ * rules as fe_apply_H per instance. */
+fe_status fe_batch_apply_H(fe_batch* batch, const void* const* X, void* const* Y,
+                           const int64_t* nvec, const int64_t* ld, fe_precision prec);
+
+/* In-place filter of every X_i with its own bounds a[i] < b[i], a0[i] (host arrays): the
+ * result equals fe_cheb_filter per instance; each of the degree steps is one launch over
+ * all instances.  Uses each mesh's filter workspace. */
+fe_status fe_batch_cheb_filter(fe_batch* batch, void* const* X, const int64_t* nvec,
+                               const int64_t* ld, int degree, const double* a,
+                               const double* b, const double* a0, fe_precision prec);
 
 typedef enum { FE_BIAS_CEF = 0, FE_BIAS_CPD = 1 } fe_bias_kind;
 

@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import (FE_BF16_F32ACC, FE_BIAS_CEF, FE_BIAS_CPD, FE_F32, FE_F32_F32ACC, FE_F64,
                    FE_FACE_DIRICHLET, FE_FACE_NEUMANN, FeError, FePoissonBC, FeSolveInfo, call)
 
-__all__ = ["Mesh", "FeError", "FE_F64", "FE_F32", "FE_BF16_F32ACC", "FE_F32_F32ACC",
+__all__ = ["Mesh", "Batch", "FeError", "FE_F64", "FE_F32", "FE_BF16_F32ACC", "FE_F32_F32ACC",
            "FE_BIAS_CEF", "FE_BIAS_CPD", "storage_dtype", "load"]
 
 load = _lib.load
@@ -76,6 +76,18 @@ class Mesh:
 
     def _f64(self, n):
         return torch.empty(n, dtype=torch.float64, device=self.device)
+
+    def set_rr_products(self, tensor_core):
+        """Rayleigh-Ritz block products for float storage: double GEMMs (False) or
+        FP32-accurate tensor-core emulation (True)."""
+        call("fe_set_option", self._h, _lib.FE_OPT_RR_PRODUCTS,
+             _lib.FE_RR_PRODUCTS_TC32 if tensor_core else _lib.FE_RR_PRODUCTS_F64)
+
+    def set_poisson_precond(self, planes):
+        """Poisson CG preconditioner: Jacobi (False) or Jacobi plus the z-plane coarse
+        solve (True, the default)."""
+        call("fe_set_option", self._h, _lib.FE_OPT_POISSON_PRECOND,
+             _lib.FE_PRECOND_JACOBI_PLANES if planes else _lib.FE_PRECOND_JACOBI)
 
     def node_coords(self):
         out = self._f64((self.n_phi, 3))
@@ -188,3 +200,51 @@ class Mesh:
         call("fe_poisson_solve", self._h, _ptr(rho), C.byref(bc), _ptr(phi), _ptr(vb),
              C.byref(info))
         return phi, vb, info
+
+
+class Batch:
+    """Independent slabs with a common p and cell size, stepped together (fe_batch_*): each
+    operator application is one kernel launch over every instance."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        arr = (C.c_void_p * len(self.meshes))(*[m.handle.value for m in self.meshes])
+        h = C.c_void_p()
+        call("fe_batch_create", arr, len(self.meshes), C.byref(h))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _lib.load().fe_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _blocks(self, Xs, prec):
+        assert len(Xs) == len(self.meshes)
+        for X, m in zip(Xs, self.meshes):
+            assert X.dtype == storage_dtype(prec) and X.is_cuda and X.shape[0] == m.n_psi
+        n = len(Xs)
+        ptrs = (C.c_void_p * n)(*[X.data_ptr() for X in Xs])
+        nvec = (C.c_int64 * n)(*[X.shape[1] for X in Xs])
+        ld = (C.c_int64 * n)(*[X.stride(0) for X in Xs])
+        return ptrs, nvec, ld
+
+    def apply_H(self, Xs, Ys=None, prec=FE_F64):
+        Ys = [torch.empty_like(X) for X in Xs] if Ys is None else Ys
+        xp, nvec, ld = self._blocks(Xs, prec)
+        yp, _, _ = self._blocks(Ys, prec)
+        call("fe_batch_apply_H", self._h, xp, yp, nvec, ld, int(prec))
+        return Ys
+
+    def cheb_filter(self, Xs, degree, a, b, a0, prec=FE_F64):
+        xp, nvec, ld = self._blocks(Xs, prec)
+        n = len(Xs)
+        dd = [(C.c_double * n)(*[float(v) for v in arr]) for arr in (a, b, a0)]
+        call("fe_batch_cheb_filter", self._h, xp, nvec, ld, int(degree), dd[0], dd[1], dd[2],
+             int(prec))
+        return Xs

@@ -13,19 +13,24 @@ FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENOCONV, FE_EBREAKDOWN, FE_ETIMEOUT, F
 FE_F64, FE_F32, FE_BF16_F32ACC, FE_F32_F32ACC = range(4)
 FE_FACE_NEUMANN, FE_FACE_DIRICHLET = 0, 1
 FE_BIAS_CEF, FE_BIAS_CPD = 0, 1
+FE_OPT_RR_PRODUCTS, FE_OPT_POISSON_PRECOND = 0, 1
+FE_RR_PRODUCTS_F64, FE_RR_PRODUCTS_TC32 = 0, 1
+FE_PRECOND_JACOBI, FE_PRECOND_JACOBI_PLANES = 0, 1
 
 STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_ENOCONV",
                 5: "FE_EBREAKDOWN", 6: "FE_ETIMEOUT", 7: "FE_EUNSUPPORTED"}
 
 # every entry point declared in include/fe.h
 EXPORTS = [
-    "fe_mesh_create", "fe_mesh_destroy", "fe_mesh_info", "fe_mesh_set_stream", "fe_node_coords",
+    "fe_mesh_create", "fe_mesh_destroy", "fe_mesh_info", "fe_mesh_set_stream", "fe_set_option",
+    "fe_node_coords",
     "fe_lumped_mass", "fe_set_atoms", "fe_set_potential", "fe_apply_H", "fe_cheb_filter",
     "fe_cheb_filter_static",
     "fe_poisson_solve", "fe_poisson_solve_load", "fe_poisson_constraints",
     "fe_poisson_apply_K", "fe_poisson_rhs",
     "fe_rayleigh_ritz", "fe_atom_fields", "fe_energy", "fe_atom_fields_vjp",
     "fe_lanczos_bounds", "fe_kernel_launches", "fe_last_error",
+    "fe_batch_create", "fe_batch_destroy", "fe_batch_apply_H", "fe_batch_cheb_filter",
 ]
 
 
@@ -68,6 +73,7 @@ def load(path=LIB_PATH):
         "fe_mesh_destroy": ([P], I),
         "fe_mesh_info": ([P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)], I),
         "fe_mesh_set_stream": ([P, P], I),
+        "fe_set_option": ([P, I, I64], I),
         "fe_node_coords": ([P, P], I),
         "fe_lumped_mass": ([P, P], I),
         "fe_set_atoms": ([P, I, P, P, D, D, D], I),
@@ -86,6 +92,10 @@ def load(path=LIB_PATH):
         "fe_energy": ([P, C.POINTER(FePoissonBC), P, C.POINTER(D), C.POINTER(D), C.POINTER(D),
                        P, P, P], I),
         "fe_atom_fields_vjp": ([P, P, P, P, P], I),
+        "fe_batch_create": ([P, I, C.POINTER(C.c_void_p)], I),
+        "fe_batch_destroy": ([P], I),
+        "fe_batch_apply_H": ([P, P, P, P, P, I], I),
+        "fe_batch_cheb_filter": ([P, P, P, P, I, P, P, P, I], I),
         "fe_kernel_launches": ([], I64),
         "fe_last_error": ([], C.c_char_p),
     }

@@ -43,18 +43,14 @@ fe_status fe_tc_apply(fe_mesh* m, const float* X, float* Y, const float* Z, int6
 fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t nvec, int64_t ld,
                      double alpha, double beta, double shift, fe_precision prec) {
   if (prec == FE_F64) {
-    KronTile t = fe_default_tile(m, true, 8, nvec);
-    KronGeom g = fe_geom(m, true, t);
     KronIO<double> io{(const double*)X, ld, (double*)Y, ld, (const double*)Z, ld, m->d_veff,
                       nvec, alpha, beta, shift};
-    return fe::kron_f64(m->coefH, g, io, t.nch, m->stream);
+    return fe::kron_f64(m->coefH, fe_geom(m, true), io, m->stream);
   }
   if (prec == FE_F32) {
-    KronTile t = fe_default_tile(m, true, 4, nvec);
-    KronGeom g = fe_geom(m, true, t);
     KronIO<float> io{(const float*)X, ld, (float*)Y, ld, (const float*)Z, ld, m->d_veff_f,
                      nvec, (float)alpha, (float)beta, (float)shift};
-    return fe::kron_f32(m->coefH, g, io, t.nch, m->stream);
+    return fe::kron_f32(m->coefH, fe_geom(m, true), io, m->stream);
   }
   return fe_tc_apply(m, (const float*)X, (float*)Y, (const float*)Z, nvec, ld, (float)alpha,
                      (float)beta, (float)shift, prec);
@@ -115,17 +111,8 @@ extern "C" fe_status fe_poisson_apply_K(fe_mesh* m, const double* x, double* y) 
     return fe_fail(FE_EINVAL, "fe_poisson_apply_K: arrays must be 8-byte aligned");
   if (x == y) return fe_fail(FE_EINVAL, "fe_poisson_apply_K: x and y must differ");
   FE_TRY(fe_activate(m));
-  KronTile t;
-  t.bx = m->nx >= 4 ? 4 : m->nx;
-  t.by = m->ny >= 4 ? 4 : m->ny;
-  t.nch = 1;
-  int64_t blocks = (int64_t)((m->nx + t.bx - 1) / t.bx) * ((m->ny + t.by - 1) / t.by);
-  int zseg = m->nz;
-  while (zseg > 2 && blocks * ((m->nz + zseg - 1) / zseg) < 2 * 152) zseg = (zseg + 1) / 2;
-  t.zseg = zseg;
-  KronGeom g = fe_geom(m, false, t);
   KronIO<double> io{x, 1, y, 1, nullptr, 1, nullptr, 1, 1.0, 0.0, 0.0};
-  return fe::kron_k1(m->coefK, g, io, 1, m->stream);
+  return fe::kron_k1(m->coefK, fe_geom(m, false), io, m->stream);
 }
 
 // ---- Lanczos ---------------------------------------------------------------------------------
@@ -222,12 +209,12 @@ extern "C" fe_status fe_lanczos_bounds(fe_mesh* m, const double* v0, int steps, 
   for (int j = 0; j < steps; ++j) {
     // f = Ht v - beta_{j-1} v_old; alpha_j = f . v; f -= alpha_j v
     FE_TRY(fe_hx_step(m, v, f, nullptr, 1, 2, 1.0, 0.0, 0.0, FE_F64));
-    if (j) k_lz_axpy<<<gb, 256, 0, st>>>(f, vold, beta + j - 1, n); fe_count_launch();
+    if (j) { k_lz_axpy<<<gb, 256, 0, st>>>(f, vold, beta + j - 1, n); fe_count_launch(); }
     FE_TRY(fe::dot_async(f, v, n, 2, part, alpha + j, st));
     k_lz_axpy<<<gb, 256, 0, st>>>(f, v, alpha + j, n); fe_count_launch();
     FE_TRY(fe::dot_async(f, f, n, 2, part, beta + j, st));
     k_sqrt<<<1, 1, 0, st>>>(beta + j); fe_count_launch();
-    if (j + 1 < steps) k_lz_shift<<<gb, 256, 0, st>>>(f, v, vold, beta + j, n); fe_count_launch();
+    if (j + 1 < steps) { k_lz_shift<<<gb, 256, 0, st>>>(f, v, vold, beta + j, n); fe_count_launch(); }
   }
   FE_CUDA(cudaGetLastError());
   std::vector<double> hs(2 * steps);

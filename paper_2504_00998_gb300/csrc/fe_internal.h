@@ -13,6 +13,7 @@
 
 #define FE_MAXP 6
 #define FE_MAXN1 (FE_MAXP + 1)
+#define FE_NWS 12   // workspace slots of a mesh
 
 // ---- error state ------------------------------------------------------------------------
 fe_status fe_fail(fe_status st, const char* fmt, ...);
@@ -89,17 +90,35 @@ struct KronIO {
   T alpha, beta, shift;      // Y = alpha (H - shift) X + beta Z
 };
 
-struct KronTile { int bx, by, zseg, nch; };
+// One instance of a batched operator launch (device-resident array, ascending cta0).
+template <typename T>
+struct KronInst {
+  KronGeom g;
+  KronIO<T> io;
+  int64_t cta0;              // first CTA of this instance in the batched 1D grid
+  int64_t nvt;               // vector tiles of this instance
+};
+
 
 // operator launchers: double with 16-byte chunks, float with 16-byte chunks, and double
 // with one element per node (single-vector Poisson operator)
+// (the tile fields of g are chosen by the launcher)
 namespace fe {
-fe_status kron_f64(const KronCoef& cf, const KronGeom& g, const KronIO<double>& io, int nch,
+fe_status kron_f64(const KronCoef& cf, const KronGeom& g, const KronIO<double>& io,
                    cudaStream_t st);
-fe_status kron_f32(const KronCoef& cf, const KronGeom& g, const KronIO<float>& io, int nch,
+fe_status kron_f32(const KronCoef& cf, const KronGeom& g, const KronIO<float>& io,
                    cudaStream_t st);
-fe_status kron_k1(const KronCoef& cf, const KronGeom& g, const KronIO<double>& io, int nch,
+fe_status kron_k1(const KronCoef& cf, const KronGeom& g, const KronIO<double>& io,
                   cudaStream_t st);
+// Batched launches: plan fills the tile fields, z segmentation, nvt and cta0 of n host
+// instances (g from fe_geom, io.nvec set) and returns the total CTA count; launch runs one
+// operator application over the device copy of those instances.
+int64_t kron_batch_plan_f64(int p, KronInst<double>* inst, int n);
+int64_t kron_batch_plan_f32(int p, KronInst<float>* inst, int n);
+fe_status kron_batch_f64(const KronCoef& cf, int p, const KronInst<double>* d_inst, int n,
+                         int64_t total_ctas, bool use_z, cudaStream_t st);
+fe_status kron_batch_f32(const KronCoef& cf, int p, const KronInst<float>* d_inst, int n,
+                         int64_t total_ctas, bool use_z, cudaStream_t st);
 }  // namespace fe
 
 // ---- the mesh ---------------------------------------------------------------------------
@@ -136,8 +155,17 @@ struct fe_mesh {
   double n_electrons = 0.0;
 
   // workspaces (grown on demand, freed with the mesh)
-  void* ws[10] = {nullptr};
-  size_t ws_bytes[10] = {0};
+  void* ws[FE_NWS] = {nullptr};
+  size_t ws_bytes[FE_NWS] = {0};
+
+  // Rayleigh-Ritz block products for float storage: 0 double GEMMs, 1 tensor-core BF16x9
+  int rr_products = 0;
+  // Poisson CG preconditioner: 0 Jacobi, 1 Jacobi plus the exact z-plane coarse solve
+  int poisson_precond = 1;
+  // cached coarse-space inverse (WS_PCOARSE): valid for the constraint set of pc_key
+  int pc_state = 0;          // 0 none, 1 valid, 2 not SPD (Jacobi only for this key)
+  int pc_nz = 0;
+  fe_poisson_bc pc_key = {};
 
   // tensor-core path: p of the uploaded cell-matrix image, pinned wait-expiry flag
   int tc_img_p = -1;
@@ -146,19 +174,15 @@ struct fe_mesh {
   cublasHandle_t cublas = nullptr;
   cusolverDnHandle_t cusolver = nullptr;
 
-  // tile choices per (precision, nvec-bucket), filled by the tuner
-  KronTile tileH[4];
-  bool tuned[4] = {false, false, false, false};
-  KronTile tileK;
 };
 
 enum { WS_CHEB = 0, WS_RR_X = 1, WS_RR_HX = 2, WS_RR_SMALL = 3, WS_CG = 4, WS_RED = 5,
-       WS_LANCZOS = 6, WS_TC = 7, WS_TC_IMG = 8, WS_YCELL = 9 };
+       WS_LANCZOS = 6, WS_TC = 7, WS_TC_IMG = 8, WS_YCELL = 9, WS_RR_TC32 = 10,
+       WS_PCOARSE = 11 };
 
 fe_status fe_ws(fe_mesh* m, int slot, size_t bytes, void** out);
 fe_status fe_activate(const fe_mesh* m);
-KronGeom fe_geom(const fe_mesh* m, bool psi, const KronTile& t);
-KronTile fe_default_tile(const fe_mesh* m, bool psi, int elem_bytes, int64_t nvec);
+KronGeom fe_geom(const fe_mesh* m, bool psi);
 
 // fields (potentials, densities) -- fe_fields.cu
 fe_status fe_fields_build(fe_mesh* m);

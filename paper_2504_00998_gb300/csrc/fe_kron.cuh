@@ -11,16 +11,24 @@
 // three-term Chebyshev update fused (S = M^-1/2, oscale = 1/2 M^-1/2), or the Poisson
 // operator K (S = I, oscale = 1, no potential).
 //
-// Work decomposition: one CTA owns an xy block of bx x by cells' nodes (half-open), a tile
-// of vectors, and a range of z layers.  It sweeps the z planes in order; each plane (with a
-// p-node halo in x and y, periodic wrap) is staged into shared memory with cp.async one
-// plane ahead, contracted in y then in x in shared memory (cell by cell, the shared
-// boundary node taking the previous cell's last row), and the two in-plane results are
-// accumulated into the p+1 output planes of the current z layer held in registers.  A
-// layer's first p planes are final once its top plane is processed; the top plane's sum
-// carries into the next layer.  No scatter, no atomics: every output node is written once
-// by the thread that owns it, so results are bitwise reproducible.
+// Work decomposition: one CTA owns the nodes of an xy block of BX x BY cells (half-open),
+// a tile of NCH vector chunks, and a range of z layers.  It sweeps the z planes in order.
+// Each plane (with a p-node periodic halo in x and y), the potential and the previous
+// Chebyshev iterate of the owned nodes are staged into shared memory with cp.async one
+// plane ahead; the plane is contracted in y then in x (cell by cell, the shared boundary
+// node taking the previous cell's last row), and the two in-plane results are accumulated
+// into the p+1 output planes of the current z layer held in registers.  A layer's first p
+// planes are final once its top plane is processed; the top plane's sum carries into the
+// next layer.  No scatter, no atomics: every output node is written once by the thread that
+// owns it, so results are bitwise reproducible.
+//
+// All tile dimensions are compile-time constants; each thread's staging addresses are
+// computed once per launch.  CTAs are small (a few hundred threads, ~50 KB of shared
+// memory) so that several share an SM and one CTA's barriers overlap another's work.
 #pragma once
+
+#include <cmath>
+#include <type_traits>
 
 #include "fe_internal.h"
 
@@ -33,7 +41,11 @@ struct KronCoefT {
   T AzK[FE_MAXN1][FE_MAXN1], AzM[FE_MAXN1][FE_MAXN1];
   T sig[FE_MAXN1];
   T wz[FE_MAXN1];
-  T zin, zout;
+  // 1/sqrt and sqrt of the z mass factor of a plane by local index (index 0: a plane shared
+  // by two cells; *_face: the bottom or top face), so that no plane pays a division
+  T rsq[FE_MAXN1], sq[FE_MAXN1];
+  T rsq_face, sq_face;
+  T zin, zout, izout;
   int mass_scale;
 };
 
@@ -51,9 +63,15 @@ inline KronCoefT<T> convert_coef(const KronCoef& c) {
     }
     o.sig[i] = (T)c.sig[i];
     o.wz[i] = (T)c.wz[i];
+    const double mz = i == 0 ? 2.0 * c.wz[0] : c.wz[i];
+    o.rsq[i] = mz > 0.0 ? (T)(1.0 / std::sqrt(mz)) : T(0);
+    o.sq[i] = (T)std::sqrt(mz > 0.0 ? mz : 0.0);
   }
+  o.rsq_face = c.wz[0] > 0.0 ? (T)(1.0 / std::sqrt(c.wz[0])) : T(0);
+  o.sq_face = (T)std::sqrt(c.wz[0] > 0.0 ? c.wz[0] : 0.0);
   o.zin = (T)c.zin;
   o.zout = (T)c.zout;
+  o.izout = (T)(1.0 / c.zout);
   o.mass_scale = c.mass_scale;
   return o;
 }
@@ -86,20 +104,22 @@ template <>
 __device__ __forceinline__ double Chunk<double, 1>::fma_t(double a, double b, double c) {
   return __fma_rn(a, b, c);
 }
-
-template <typename T, int CH>
-__device__ __forceinline__ Chunk<T, CH> lds(const Chunk<T, CH>* p) {
-  return *p;
+template <>
+__device__ __forceinline__ float Chunk<float, 1>::fma_t(float a, float b, float c) {
+  return __fmaf_rn(a, b, c);
 }
 
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int nbytes_valid,
-                                         int chunk_bytes) {
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int nbytes_valid) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  if (chunk_bytes == 16) {
+  if constexpr (BYTES == 16) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
                  "r"(nbytes_valid));
-  } else {
+  } else if constexpr (BYTES == 8) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem),
+                 "r"(nbytes_valid));
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem),
                  "r"(nbytes_valid));
   }
 }
@@ -114,101 +134,171 @@ __device__ __forceinline__ int pmod(int a, int n) {
   return r < 0 ? r + n : r;
 }
 
-template <typename T, int P, int CH, int IPT>
-__global__ void __launch_bounds__(512)
-kron_kernel(const KronCoefT<T> cf, const KronGeom g, const KronIO<T> io, const int nch) {
-  using C = Chunk<T, CH>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int BXn = g.bx * P, BYn = g.by * P;
-  const int BXH = BXn + P + 1, BYH = BYn + P + 1;
-  C* stage0 = reinterpret_cast<C*>(smem_raw);
-  const int stage_sz = BYH * BXH * nch;
-  C* A = stage0 + 2 * stage_sz;
-  C* B = A + BYn * BXH * nch;
-  C* W1 = B + BYn * BXH * nch;
-  C* W2 = W1 + BYn * BXn * nch;
+// compile-time tile shape
+template <int P_, int BX_, int BY_, int NCH_, int NTHR_>
+struct KronTileT {
+  static constexpr int P = P_, BX = BX_, BY = BY_, NCH = NCH_, NTHR = NTHR_;
+  static constexpr int BXn = BX * P, BYn = BY * P;
+  static constexpr int BXH = BXn + P + 1, BYH = BYn + P + 1;
+  static constexpr int NZI = BXn * BYn * NCH;            // output items (node, chunk)
+  static constexpr int IPT = (NZI + NTHR - 1) / NTHR;    // output items per thread
+  static constexpr int NST = BYH * BXH * NCH;            // staged chunks per plane
+  static constexpr int SPT = (NST + NTHR - 1) / NTHR;    // staged chunks per thread
+  static constexpr int NYI = BXH * NCH * BY;             // y-phase items (cell segments)
+  static constexpr int NXI = BYn * NCH * BX;             // x-phase items (cell segments)
+  static constexpr int ZR = P + 2;                       // ring of staged Chebyshev planes
+  // stage (and V) slots: plane gz + 2 is staged while other threads may still read plane gz
+  // after the plane's last barrier, so three slots keep those reads race-free
+  static constexpr int NSB = 3;
+  // row strides (in nodes) of the in-plane intermediates, odd so that the x phase's
+  // column-wise accesses (consecutive threads on consecutive rows) fall in distinct banks
+  static constexpr int ARS = BXH | 1;
+  static constexpr int WRS = BXn | 1;
+};
 
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int bxi = blockIdx.x % g.nbx, byi = blockIdx.x / g.nbx;
+// One CTA's work: xy block bxy (x fastest), vector tile vti, z segment zsi.
+template <typename T, int CH, class TL>
+__device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom& g,
+                                          const KronIO<T>& io, int bxy, int vti, int zsi) {
+  using C = Chunk<T, CH>;
+  constexpr int P = TL::P, NCH = TL::NCH, BXn = TL::BXn, BYn = TL::BYn;
+  constexpr int BXH = TL::BXH, NTHR = TL::NTHR, IPT = TL::IPT;
+  constexpr int ARS = TL::ARS, WRS = TL::WRS;
+  constexpr int NZI = TL::NZI, NST = TL::NST, SPT = TL::SPT;
+  constexpr int CHB = CH * (int)sizeof(T);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* stage0 = reinterpret_cast<C*>(smem_raw);                  // [NSB][BYH][BXH][NCH]
+  C* A = stage0 + TL::NSB * NST;                               // [BYn][ARS][NCH]
+  C* B = A + BYn * ARS * NCH;
+  C* W1 = B + BYn * ARS * NCH;                                 // [BYn][WRS][NCH]
+  C* W2 = W1 + BYn * WRS * NCH;
+  C* Zr = W2 + BYn * WRS * NCH;                                // [ZR][BYn][BXn][NCH]
+  const bool use_z = io.Z != nullptr;                          // (beta != 0 by launch)
+  const bool use_v = io.V != nullptr;
+  T* Vs = reinterpret_cast<T*>(Zr + (use_z ? TL::ZR * NZI : 0));   // [NSB][BYn][BXn]
+
+  const int tid = threadIdx.x;
+  const int bxi = bxy % g.nbx, byi = bxy / g.nbx;
   const int x0 = bxi * BXn, y0 = byi * BYn;
-  const int64_t vt0 = (int64_t)blockIdx.y * nch * CH;
-  const int c0 = blockIdx.z * g.zseg;
+  const int64_t vt0 = (int64_t)vti * NCH * CH;
+  const int c0 = zsi * g.zseg;
   const int c1 = min(c0 + g.zseg, g.nz);
   const int cb = c0 > 0 ? c0 - 1 : 0;
   const int gbeg = cb * P, gend = c1 * P;
-  const int nitemsZ = BXn * BYn * nch;
+  const int64_t plane_nodes = (int64_t)g.NX * g.NY;
 
-  // ---- the thread's output items --------------------------------------------------------
+  // ---- staging addresses (per thread, once) ---------------------------------------------
+  int64_t s_goff[SPT];
+  int s_bytes[SPT];
+#pragma unroll
+  for (int i = 0; i < SPT; ++i) {
+    const int e = tid + i * NTHR;
+    const int ec = e < NST ? e : 0;
+    const int ch = ec % NCH, node = ec / NCH;
+    const int xh = node % BXH, yh = node / BXH;
+    const int gx = pmod(x0 - P + xh, g.NX), gy = pmod(y0 - P + yh, g.NY);
+    const int64_t v0 = vt0 + (int64_t)ch * CH;
+    const int64_t rem = io.nvec - v0;
+    s_bytes[i] = e >= NST ? -1 : (rem <= 0 ? 0 : (rem >= CH ? CHB : (int)(rem * sizeof(T))));
+    s_goff[i] = (gx + (int64_t)g.NX * gy) * io.ldx + v0;
+  }
+
+  // ---- the thread's output items ---------------------------------------------------------
   int it_x[IPT], it_y[IPT], it_ch[IPT];
   bool it_own[IPT];
-  T it_sxy[IPT];
+  int64_t it_node[IPT];     // in-plane node index of the output
+  T it_sxy[IPT], it_isxy[IPT];
   C acc[IPT][P + 1];
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
-    int item = tid + i * nthr;
-    bool valid = item < nitemsZ;
-    int itc = valid ? item : 0;
-    it_ch[i] = itc % nch;
-    int node = itc / nch;
+    const int item = tid + i * NTHR;
+    const bool valid = item < NZI;
+    const int itc = valid ? item : 0;
+    it_ch[i] = itc % NCH;
+    const int node = itc / NCH;
     it_x[i] = node % BXn;
     it_y[i] = node / BXn;
-    int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
+    const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
     it_own[i] = valid && (x0 + it_x[i] < g.NX) && (y0 + it_y[i] < g.NY) && (v0 < io.nvec);
+    it_node[i] = (x0 + it_x[i]) + (int64_t)g.NX * (y0 + it_y[i]);
     it_sxy[i] = cf.mass_scale ? cf.sig[it_x[i] % P] * cf.sig[it_y[i] % P] : T(1);
+    it_isxy[i] = T(1) / it_sxy[i];
 #pragma unroll
     for (int j = 0; j <= P; ++j) acc[i][j].zero();
   }
 
-  const int chunk_bytes = (int)(CH * sizeof(T));
-  auto stage_plane = [&](int gz, C* dst) {
-    int zs = gz - g.gz_lo;
-    if (zs < 0 || zs >= g.NZs) return;
-    const int total = BYH * BXH * nch;
-    for (int e = tid; e < total; e += nthr) {
-      int ch = e % nch;
-      int node = e / nch;
-      int xh = node % BXH, yh = node / BXH;
-      int gx = pmod(x0 - P + xh, g.NX);
-      int gy = pmod(y0 - P + yh, g.NY);
-      int64_t nid = gx + (int64_t)g.NX * (gy + (int64_t)g.NY * zs);
-      int64_t v0 = vt0 + (int64_t)ch * CH;
-      int64_t rem = io.nvec - v0;
-      int valid = rem <= 0 ? 0 : (rem >= CH ? chunk_bytes : (int)(rem * sizeof(T)));
-      const T* src = valid ? io.X + nid * io.ldx + v0 : io.X;
-      cp_async(dst + e, src, valid, chunk_bytes);
-    }
+  auto stored = [&](int gz) { return gz - g.gz_lo >= 0 && gz - g.gz_lo < g.NZs; };
+  // 1/sqrt(mz) and sqrt(mz) of plane gz (1 for the plain stiffness)
+  auto rsq_of = [&](int gz) -> T {
+    if (!cf.mass_scale) return T(1);
+    const int l = gz % P;
+    if (l != 0) return cf.rsq[l];
+    return (gz == 0 || gz == g.nz * P) ? cf.rsq_face : cf.rsq[0];
+  };
+  auto sq_of = [&](int gz) -> T {
+    if (!cf.mass_scale) return T(1);
+    const int l = gz % P;
+    if (l != 0) return cf.sq[l];
+    return (gz == 0 || gz == g.nz * P) ? cf.sq_face : cf.sq[0];
+  };
+  auto owned_plane = [&](int gz) {   // planes this segment writes
+    return stored(gz) && ((gz >= c0 * P && gz < c1 * P) || (gz == g.nz * P && c1 == g.nz));
   };
 
-  auto mz_of = [&](int gz) -> T {
-    int l = gz % P;
-    if (l != 0) return cf.wz[l];
-    return (gz == 0 || gz == g.nz * P) ? cf.wz[0] : T(2) * cf.wz[0];
+  // stage plane gz: the halo block of X into the stage buffer, V and the Chebyshev operand
+  // of the owned nodes into their rings
+  auto stage_plane = [&](int gz) {
+    if (!stored(gz)) return;
+    const int zs = gz - g.gz_lo;
+    const int64_t pbase = (int64_t)zs * plane_nodes * io.ldx;
+    C* dst = stage0 + ((gz - gbeg) % TL::NSB) * NST;
+#pragma unroll
+    for (int i = 0; i < SPT; ++i) {
+      const int e = tid + i * NTHR;
+      if (s_bytes[i] > 0) cp_async<CHB>(dst + e, io.X + pbase + s_goff[i], s_bytes[i]);
+      else if (s_bytes[i] == 0) cp_async<CHB>(dst + e, io.X, 0);
+    }
+    if (use_v && tid < BXn * BYn) {
+      const int x = tid % BXn, y = tid / BXn;
+      T* vd = Vs + ((gz - gbeg) % TL::NSB) * (BXn * BYn) + tid;
+      const bool ok = x0 + x < g.NX && y0 + y < g.NY;
+      const int64_t nid = (int64_t)zs * plane_nodes + (x0 + x) + (int64_t)g.NX * (y0 + y);
+      cp_async<(int)sizeof(T)>(vd, ok ? io.V + nid : io.V, ok ? (int)sizeof(T) : 0);
+    }
+    if (use_z && owned_plane(gz)) {
+      C* zd = Zr + (gz % TL::ZR) * NZI;
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        const int item = tid + i * NTHR;
+        if (item >= NZI) continue;
+        const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
+        const int64_t rem = io.nvec - v0;
+        const int nb = (!it_own[i] || rem <= 0) ? 0 : (rem >= CH ? CHB : (int)(rem * sizeof(T)));
+        const T* src = nb ? io.Z + ((int64_t)zs * plane_nodes + it_node[i]) * io.ldz + v0 : io.Z;
+        cp_async<CHB>(zd + item, src, nb);
+      }
+    }
   };
 
   // write the final value of output plane gzo held in acc[i][j]
   auto write_plane = [&](int gzo, int j) {
-    int zs = gzo - g.gz_lo;
-    if (zs < 0 || zs >= g.NZs) return;
-    T ps = cf.mass_scale ? cf.zout / sqrt(mz_of(gzo)) : cf.zout;
+    if (!owned_plane(gzo)) return;
+    const int zs = gzo - g.gz_lo;
+    const T ps = cf.zout * rsq_of(gzo);
+    const C* zsrc = Zr + (gzo % TL::ZR) * NZI;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       if (!it_own[i]) continue;
-      int64_t nid = (x0 + it_x[i]) + (int64_t)g.NX * ((y0 + it_y[i]) + (int64_t)g.NY * zs);
-      int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
-      T sc = io.alpha * ps * it_sxy[i];
+      const int64_t nid = (int64_t)zs * plane_nodes + it_node[i];
+      const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
+      const T sc = io.alpha * ps * it_sxy[i];
       C out;
 #pragma unroll
       for (int e = 0; e < CH; ++e) out.v[e] = sc * acc[i][j].v[e];
-      if (io.Z != nullptr && io.beta != T(0)) {
-        const T* zp = io.Z + nid * io.ldz + v0;
-        if (v0 + CH <= io.nvec) {
-          C zc = *reinterpret_cast<const C*>(zp);
+      if (use_z) {
+        const C zc = zsrc[tid + i * NTHR];
 #pragma unroll
-          for (int e = 0; e < CH; ++e) out.v[e] = C::fma_t(io.beta, zc.v[e], out.v[e]);
-        } else {
-          for (int e = 0; e < CH; ++e)
-            if (v0 + e < io.nvec) out.v[e] = C::fma_t(io.beta, zp[e], out.v[e]);
-        }
+        for (int e = 0; e < CH; ++e) out.v[e] = C::fma_t(io.beta, zc.v[e], out.v[e]);
       }
       T* yp = io.Y + nid * io.ldy + v0;
       if (v0 + CH <= io.nvec) {
@@ -220,129 +310,137 @@ kron_kernel(const KronCoefT<T> cf, const KronGeom g, const KronIO<T> io, const i
     }
   };
 
-  // z contraction of the current plane's in-plane results into the layer accumulators
-  auto phase_z = [&](int k, T s_in, const C* w1, const C* w2) {
+  // Plane with local index K (compile time, so every coefficient is an immediate operand):
+  // the potential term of the plane's own nodes (when pot) and the z contraction of its
+  // in-plane results into the layer accumulators.
+  auto plane_z = [&](auto kc, bool pot, T s_in, T inv_ps, const T* vv, const C* st,
+                     const C* w1, const C* w2) {
+    constexpr int K = decltype(kc)::value;
+    if constexpr (K <= P) {
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        if (pot && it_own[i]) {
+          const T pv = (vv[it_y[i] * BXn + it_x[i]] - io.shift) * inv_ps * it_isxy[i];
+          const C xs = st[((it_y[i] + P) * BXH + (it_x[i] + P)) * NCH + it_ch[i]];
+          acc[i][K].fma(pv, xs);
+        }
+        C a = w1[i], b = w2[i];
+#pragma unroll
+        for (int e = 0; e < CH; ++e) { a.v[e] *= s_in; b.v[e] *= s_in; }
+#pragma unroll
+        for (int j = 0; j <= P; ++j) {
+          acc[i][j].fma(cf.AzK[j][K], a);
+          acc[i][j].fma(cf.AzM[j][K], b);
+        }
+      }
+    }
+  };
+  auto dispatch_z = [&](int k, bool pot, T s_in, T inv_ps, const T* vv, const C* st,
+                        const C* w1, const C* w2) {
+    switch (k) {
+      case 0: plane_z(std::integral_constant<int, 0>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
+      case 1: plane_z(std::integral_constant<int, 1>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
+      case 2: plane_z(std::integral_constant<int, 2>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
+      case 3: plane_z(std::integral_constant<int, 3>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
+      case 4: plane_z(std::integral_constant<int, 4>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
+      case 5: plane_z(std::integral_constant<int, 5>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
+      case 6: plane_z(std::integral_constant<int, 6>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
+      default: break;
+    }
+  };
+
+  auto shift_layer = [&]() {
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
-      C a = w1[i], b = w2[i];
+      acc[i][0] = acc[i][P];
 #pragma unroll
-      for (int e = 0; e < CH; ++e) { a.v[e] *= s_in; b.v[e] *= s_in; }
-#pragma unroll
-      for (int j = 0; j <= P; ++j) {
-        // k is uniform across the block; the table lookups are constant-bank reads
-        T ck, cm;
-        switch (k) {
-#define FE_ZCASE(kk) \
-  case kk:           \
-    if (kk <= P) { ck = cf.AzK[j][kk]; cm = cf.AzM[j][kk]; } else { ck = cm = T(0); } break;
-          FE_ZCASE(0) FE_ZCASE(1) FE_ZCASE(2) FE_ZCASE(3) FE_ZCASE(4) FE_ZCASE(5) FE_ZCASE(6)
-#undef FE_ZCASE
-          default: ck = cm = T(0);
-        }
-        acc[i][j].fma(ck, a);
-        acc[i][j].fma(cm, b);
-      }
+      for (int j = 1; j <= P; ++j) acc[i][j].zero();
     }
   };
 
   // ---- sweep -----------------------------------------------------------------------------
-  stage_plane(gbeg, stage0);
+  stage_plane(gbeg);
   cp_commit();
   int c = cb;
   for (int gz = gbeg; gz <= gend; ++gz) {
     const int k = gz - c * P;
-    C* st = stage0 + ((gz - gbeg) & 1) * stage_sz;
     if (gz < gend) {
-      stage_plane(gz + 1, stage0 + ((gz + 1 - gbeg) & 1) * stage_sz);
+      stage_plane(gz + 1);
       cp_commit();
       cp_wait<1>();
     } else {
       cp_wait<0>();
     }
     __syncthreads();
+    const C* st = stage0 + ((gz - gbeg) % TL::NSB) * NST;
 
-    const int zs = gz - g.gz_lo;
-    const bool stored = zs >= 0 && zs < g.NZs;
-    C w1[IPT], w2[IPT];
-    if (stored) {
-      const T pscale = cf.mass_scale ? cf.zout / sqrt(mz_of(gz)) : cf.zout;
-      // potential term folded into the accumulator of this plane (k = 0..P of layer c)
-      if (io.V != nullptr) {
+    if (stored(gz)) {
+      // The two in-plane phases run on scalar lanes: an item is one cell segment of one
+      // vector entry, so that every thread has work (a chunk-wide item would leave most of
+      // the CTA idle at the following barrier).  NL scalars per node, lane-fastest indexing
+      // keeps consecutive threads on consecutive words.
+      using S1 = Chunk<T, 1>;
+      constexpr int NL = NCH * CH;
+      const S1* sts = reinterpret_cast<const S1*>(st);
+      S1* As = reinterpret_cast<S1*>(A);
+      S1* Bs = reinterpret_cast<S1*>(B);
+      // phase Y: a = AyM U, b = AyK U along y for every halo x
+#pragma unroll 1
+      for (int e = tid; e < TL::NYI * CH; e += NTHR) {
+        const int l = e % NL;
+        const int r = e / NL;
+        const int xh = r % BXH;
+        const int yb = (r / BXH) * P;
+        S1 own[P + 1], prv[P];
 #pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-          if (!it_own[i]) continue;
-          int64_t nid = (x0 + it_x[i]) + (int64_t)g.NX * ((y0 + it_y[i]) + (int64_t)g.NY * zs);
-          T vv = (io.V[nid] - io.shift) / (pscale * it_sxy[i]);
-          const C xs = st[((it_y[i] + P) * BXH + (it_x[i] + P)) * nch + it_ch[i]];
-          switch (k) {
-#define FE_PCASE(kk) \
-  case kk:           \
-    if (kk <= P) acc[i][kk].fma(vv, xs); break;
-            FE_PCASE(0) FE_PCASE(1) FE_PCASE(2) FE_PCASE(3) FE_PCASE(4) FE_PCASE(5) FE_PCASE(6)
-#undef FE_PCASE
-            default: break;
+        for (int kk = 0; kk <= P; ++kk) own[kk] = sts[((yb + P + kk) * BXH + xh) * NL + l];
+#pragma unroll
+        for (int kk = 0; kk < P; ++kk) prv[kk] = sts[((yb + kk) * BXH + xh) * NL + l];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          S1 a, b;
+          a.zero();
+          b.zero();
+#pragma unroll
+          for (int kk = 0; kk <= P; ++kk) {
+            a.fma(cf.AyM[j][kk], own[kk]);
+            b.fma(cf.AyK[j][kk], own[kk]);
           }
-        }
-      }
-      // phase Y: a = AyM U, b = AyK U along y at every halo x, cell by cell
-      {
-        const int cnt = BXH * nch * g.by;
-        for (int e = tid; e < cnt; e += nthr) {
-          int ch = e % nch;
-          int r = e / nch;
-          int xh = r % BXH;
-          int cyl = r / BXH;
-          int yb = cyl * P;
-          C own[P + 1], prv[P];
+          if (j == 0) {
 #pragma unroll
-          for (int kk = 0; kk <= P; ++kk) own[kk] = st[((yb + P + kk) * BXH + xh) * nch + ch];
-#pragma unroll
-          for (int kk = 0; kk < P; ++kk) prv[kk] = st[((yb + kk) * BXH + xh) * nch + ch];
-#pragma unroll
-          for (int j = 0; j < P; ++j) {
-            C a, b;
-            a.zero();
-            b.zero();
-#pragma unroll
-            for (int kk = 0; kk <= P; ++kk) {
-              a.fma(cf.AyM[j][kk], own[kk]);
-              b.fma(cf.AyK[j][kk], own[kk]);
+            for (int kk = 0; kk < P; ++kk) {
+              a.fma(cf.AyM[P][kk], prv[kk]);
+              b.fma(cf.AyK[P][kk], prv[kk]);
             }
-            if (j == 0) {
-#pragma unroll
-              for (int kk = 0; kk < P; ++kk) {
-                a.fma(cf.AyM[P][kk], prv[kk]);
-                b.fma(cf.AyK[P][kk], prv[kk]);
-              }
-              a.fma(cf.AyM[P][P], own[0]);
-              b.fma(cf.AyK[P][P], own[0]);
-            }
-            A[((yb + j) * BXH + xh) * nch + ch] = a;
-            B[((yb + j) * BXH + xh) * nch + ch] = b;
+            a.fma(cf.AyM[P][P], own[0]);
+            b.fma(cf.AyK[P][P], own[0]);
           }
+          As[((yb + j) * ARS + xh) * NL + l] = a;
+          Bs[((yb + j) * ARS + xh) * NL + l] = b;
         }
       }
       __syncthreads();
-      // phase X: W1 = AxM a, W2 = AxK a + AxM b along x at every owned y
+      // phase X: W1 = AxM a, W2 = AxK a + AxM b along x for every owned y
       {
-        const int cnt = BYn * nch * g.bx;
-        for (int e = tid; e < cnt; e += nthr) {
-          int ch = e % nch;
-          int r = e / nch;
-          int y = r % BYn;
-          int cxl = r / BYn;
-          int xb = cxl * P;
-          const C* arow = A + (size_t)y * BXH * nch;
-          const C* brow = B + (size_t)y * BXH * nch;
-          C ao[P + 1], bo[P + 1];
+        S1* W1s = reinterpret_cast<S1*>(W1);
+        S1* W2s = reinterpret_cast<S1*>(W2);
+#pragma unroll 1
+        for (int e = tid; e < TL::NXI * CH; e += NTHR) {
+          const int l = e % NL;
+          const int r = e / NL;
+          const int y = r % BYn;
+          const int xb = (r / BYn) * P;
+          const S1* arow = As + y * ARS * NL;
+          const S1* brow = Bs + y * ARS * NL;
+          S1 ao[P + 1], bo[P + 1];
 #pragma unroll
           for (int kk = 0; kk <= P; ++kk) {
-            ao[kk] = arow[(xb + P + kk) * nch + ch];
-            bo[kk] = brow[(xb + P + kk) * nch + ch];
+            ao[kk] = arow[(xb + P + kk) * NL + l];
+            bo[kk] = brow[(xb + P + kk) * NL + l];
           }
 #pragma unroll
           for (int j = 0; j < P; ++j) {
-            C u, v;
+            S1 u, v;
             u.zero();
             v.zero();
 #pragma unroll
@@ -354,8 +452,8 @@ kron_kernel(const KronCoefT<T> cf, const KronGeom g, const KronIO<T> io, const i
             if (j == 0) {
 #pragma unroll
               for (int kk = 0; kk < P; ++kk) {
-                C ap = arow[(xb + kk) * nch + ch];
-                C bp = brow[(xb + kk) * nch + ch];
+                const S1 ap = arow[(xb + kk) * NL + l];
+                const S1 bp = brow[(xb + kk) * NL + l];
                 u.fma(cf.AxM[P][kk], ap);
                 v.fma(cf.AxK[P][kk], ap);
                 v.fma(cf.AxM[P][kk], bp);
@@ -364,83 +462,260 @@ kron_kernel(const KronCoefT<T> cf, const KronGeom g, const KronIO<T> io, const i
               v.fma(cf.AxK[P][P], ao[0]);
               v.fma(cf.AxM[P][P], bo[0]);
             }
-            W1[(y * BXn + xb + j) * nch + ch] = u;
-            W2[(y * BXn + xb + j) * nch + ch] = v;
+            W1s[(y * WRS + xb + j) * NL + l] = u;
+            W2s[(y * WRS + xb + j) * NL + l] = v;
           }
         }
       }
       __syncthreads();
+      C w1[IPT], w2[IPT];
 #pragma unroll
       for (int i = 0; i < IPT; ++i) {
-        int item = (it_y[i] * BXn + it_x[i]) * nch + it_ch[i];
+        const int item = (it_y[i] * WRS + it_x[i]) * NCH + it_ch[i];
         w1[i] = W1[item];
         w2[i] = W2[item];
       }
-      const T s_in = cf.mass_scale ? cf.zin / sqrt(mz_of(gz)) : cf.zin;
-      phase_z(k, s_in, w1, w2);
+      const T s_in = cf.zin * rsq_of(gz);
+      const T inv_ps = sq_of(gz) * cf.izout;
+      const T* vv = Vs + ((gz - gbeg) % TL::NSB) * (BXn * BYn);
+      dispatch_z(k, use_v, s_in, inv_ps, vv, st, w1, w2);
       if (k == P) {
         // the layer is complete: its first P planes are final; the top plane's sum
         // becomes the bottom accumulator of the next layer
-        if (c >= c0) {
 #pragma unroll
-          for (int j = 0; j < P; ++j) write_plane(c * P + j, j);
-        }
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-          acc[i][0] = acc[i][P];
-#pragma unroll
-          for (int j = 1; j <= P; ++j) acc[i][j].zero();
-        }
+        for (int j = 0; j < P; ++j) write_plane(c * P + j, j);
+        shift_layer();
         ++c;
-        if (c < c1) phase_z(0, s_in, w1, w2);
+        if (c < c1) dispatch_z(0, false, s_in, inv_ps, vv, st, w1, w2);
       }
-    } else {
+    } else if (k == P) {
       // an unstored (homogeneous Dirichlet) plane contributes nothing
-      if (k == P) {
-        if (c >= c0) {
 #pragma unroll
-          for (int j = 0; j < P; ++j) write_plane(c * P + j, j);
-        }
-#pragma unroll
-        for (int i = 0; i < IPT; ++i) {
-          acc[i][0] = acc[i][P];
-#pragma unroll
-          for (int j = 1; j <= P; ++j) acc[i][j].zero();
-        }
-        ++c;
-      }
+      for (int j = 0; j < P; ++j) write_plane(c * P + j, j);
+      shift_layer();
+      ++c;
     }
   }
   // the last processed plane (gend = c1 P) is final only if it is the top face
-  if (c1 == g.nz) write_plane(gend, 0);
+  write_plane(gend, 0);
 }
 
-template <typename T, int P, int CH, int IPT>
-fe_status kron_launch_t(const KronCoef& cf, const KronGeom& g, const KronIO<T>& io, int nch,
-                        cudaStream_t st) {
-  const int BXn = g.bx * P, BYn = g.by * P;
-  const int BXH = BXn + P + 1, BYH = BYn + P + 1;
-  const int nitemsZ = BXn * BYn * nch;
-  int nthr = ((nitemsZ + IPT - 1) / IPT + 31) / 32 * 32;
-  if (nthr > 512) return fe_fail(FE_EINVAL, "tile too large for one CTA");
-  size_t smem = sizeof(Chunk<T, CH>) * (size_t)nch *
-                (2 * (size_t)BYH * BXH + 2 * (size_t)BYn * BXH + 2 * (size_t)BYn * BXn);
-  if (smem > 227 * 1024) return fe_fail(FE_EINVAL, "tile needs %zu bytes of shared memory", smem);
-  auto kern = kron_kernel<T, P, CH, IPT>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return fe_fail(FE_ECUDA, "smem attribute: %s", cudaGetErrorString(e));
+// 1D grid, vector tile fastest: the CTAs that read the other halves of a node's DRAM
+// bursts (neighbouring vector tiles of the same xy block) run side by side, so a burst is
+// fetched once; neighbouring xy blocks (halo sharing) follow within the resident window.
+template <typename T, int CH, class TL>
+__global__ void __launch_bounds__(TL::NTHR)
+kron_kernel(const KronCoefT<T> cf, const KronGeom g, const KronIO<T> io, int nvt) {
+  const int b = blockIdx.x;
+  const int nxy = g.nbx * g.nby;
+  const int r = b / nvt;
+  kron_body<T, CH, TL>(cf, g, io, r % nxy, b % nvt, r / nxy);
+}
+
+// Batched form: many independent meshes that share p and the cell size (so one coefficient
+// table) in one launch.  The 1D grid concatenates the instances' CTA grids; a CTA finds its
+// instance by binary search over the ascending first-CTA offsets.
+template <typename T, int CH, class TL>
+__global__ void __launch_bounds__(TL::NTHR)
+kron_batch_kernel(const KronCoefT<T> cf, const KronInst<T>* __restrict__ inst, int ninst) {
+  const int64_t b = blockIdx.x;
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (inst[mid].cta0 <= b) lo = mid; else hi = mid - 1;
   }
-  int64_t vtile = (int64_t)nch * CH;
-  dim3 grid(g.nbx * g.nby, (unsigned)((io.nvec + vtile - 1) / vtile),
-            (unsigned)((g.nz + g.zseg - 1) / g.zseg));
-  if (grid.y > 65535 || grid.z > 65535) return fe_fail(FE_EINVAL, "grid too large");
+  const KronGeom g = inst[lo].g;
+  const KronIO<T> io = inst[lo].io;
+  const int64_t local = b - inst[lo].cta0;
+  const int nxy = g.nbx * g.nby;
+  const int64_t nvt = inst[lo].nvt;
+  const int64_t r = local / nvt;
+  kron_body<T, CH, TL>(cf, g, io, (int)(r % nxy), (int)(local % nvt), (int)(r / nxy));
+}
+
+// Dynamic shared memory limit, and the largest shared-memory carveout so that the residency
+// of these kernels is set by registers and their own shared memory, not by the L1 split.
+template <typename K>
+inline fe_status kron_func_setup(K kern, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fe_fail(FE_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+  }
+  return FE_OK;
+}
+
+// shared memory of one CTA
+template <typename T, int CH, class TL>
+inline size_t kron_smem(bool use_z, bool use_v) {
+  const size_t cb = sizeof(Chunk<T, CH>);
+  size_t s = cb * (TL::NSB * (size_t)TL::NST + 2 * (size_t)TL::BYn * TL::ARS * TL::NCH +
+                   2 * (size_t)TL::BYn * TL::WRS * TL::NCH);
+  if (use_z) s += cb * TL::ZR * (size_t)TL::NZI;
+  if (use_v) s += sizeof(T) * TL::NSB * (size_t)TL::BXn * TL::BYn;
+  return s;
+}
+
+template <typename T, int CH, class TL>
+fe_status kron_launch_t(const KronCoef& cf, const KronGeom& g, const KronIO<T>& io,
+                        cudaStream_t st) {
+  if (g.bx != TL::BX || g.by != TL::BY) return fe_fail(FE_EINVAL, "tile shape mismatch");
+  KronIO<T> io2 = io;
+  if (io2.Z != nullptr && io2.beta == T(0)) io2.Z = nullptr;
+  const size_t smem = kron_smem<T, CH, TL>(io2.Z != nullptr, io2.V != nullptr);
+  if (smem > 227 * 1024) return fe_fail(FE_EINVAL, "tile needs %zu bytes of shared memory", smem);
+  auto kern = kron_kernel<T, CH, TL>;
+  FE_TRY(kron_func_setup(kern, smem));
+  const int64_t vtile = (int64_t)TL::NCH * CH;
+  const int64_t nvt = (io.nvec + vtile - 1) / vtile;
+  const int64_t total = (int64_t)g.nbx * g.nby * nvt * ((g.nz + g.zseg - 1) / g.zseg);
+  if (total > 0x7fffffffLL || nvt > 0x7fffffffLL) return fe_fail(FE_EINVAL, "grid too large");
   KronCoefT<T> cft = convert_coef<T>(cf);
-  kern<<<grid, nthr, smem, st>>>(cft, g, io, nch); fe_count_launch();
+  kern<<<(unsigned)total, TL::NTHR, smem, st>>>(cft, g, io2, (int)nvt); fe_count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fe_fail(FE_ECUDA, "kron kernel launch: %s", cudaGetErrorString(e));
   return FE_OK;
+}
+
+// cells per block side for each p: about ten nodes per side
+template <int P>
+struct KronBlock {
+  static constexpr int B = P == 1 ? 8 : P == 2 ? 5 : P == 3 ? 3 : 2;
+};
+
+template <int P, int NCH>
+struct KronTileFor {
+  static constexpr int B = KronBlock<P>::B;
+  static constexpr int N = B * P * B * P * NCH;
+  static constexpr int NTHR = (N + 31) / 32 * 32 > 512 ? 512 : (N + 31) / 32 * 32;
+  using type = KronTileT<P, B, B, NCH, NTHR>;
+};
+
+}  // namespace fe
+
+namespace fe {
+
+inline int device_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  return sms;
+}
+
+// fill the block grid and the z segmentation for tile TL, then launch
+template <typename T, int CH, class TL>
+fe_status kron_go(const KronCoef& cf, KronGeom g, const KronIO<T>& io, cudaStream_t st) {
+  g.bx = TL::BX;
+  g.by = TL::BY;
+  const int nx = g.NX / g.p, ny = g.NY / g.p;
+  g.nbx = (nx + TL::BX - 1) / TL::BX;
+  g.nby = (ny + TL::BY - 1) / TL::BY;
+  const int64_t vt = (io.nvec + (int64_t)TL::NCH * CH - 1) / ((int64_t)TL::NCH * CH);
+  const int64_t base = (int64_t)g.nbx * g.nby * vt;
+  const int64_t want = 4 * (int64_t)device_sms();
+  int zseg = g.nz;
+  while (zseg > 2 && base * ((g.nz + zseg - 1) / zseg) < want) zseg = (zseg + 1) / 2;
+  g.zseg = zseg;
+  return kron_launch_t<T, CH, TL>(cf, g, io, st);
+}
+
+// batched plan: every instance gets tile TL; z segments are split (uniformly) only while the
+// whole batch has fewer than four CTAs per SM
+template <typename T, int CH, class TL>
+int64_t kron_batch_plan_t(KronInst<T>* inst, int n) {
+  int nzmax = 1;
+  for (int i = 0; i < n; ++i) {
+    KronGeom& g = inst[i].g;
+    g.bx = TL::BX;
+    g.by = TL::BY;
+    g.nbx = (g.NX / g.p + TL::BX - 1) / TL::BX;
+    g.nby = (g.NY / g.p + TL::BY - 1) / TL::BY;
+    inst[i].nvt = (inst[i].io.nvec + (int64_t)TL::NCH * CH - 1) / ((int64_t)TL::NCH * CH);
+    nzmax = g.nz > nzmax ? g.nz : nzmax;
+  }
+  const int64_t want = 4 * (int64_t)device_sms();
+  auto total_for = [&](int zseg) {
+    int64_t t = 0;
+    for (int i = 0; i < n; ++i) {
+      const KronGeom& g = inst[i].g;
+      t += (int64_t)g.nbx * g.nby * inst[i].nvt * ((g.nz + zseg - 1) / zseg);
+    }
+    return t;
+  };
+  int zseg = nzmax;
+  while (zseg > 2 && total_for(zseg) < want) zseg = (zseg + 1) / 2;
+  int64_t cta = 0;
+  for (int i = 0; i < n; ++i) {
+    KronGeom& g = inst[i].g;
+    g.zseg = zseg;
+    inst[i].cta0 = cta;
+    cta += (int64_t)g.nbx * g.nby * inst[i].nvt * ((g.nz + zseg - 1) / zseg);
+  }
+  return cta;
+}
+
+template <typename T, int CH, class TL>
+fe_status kron_batch_launch_t(const KronCoef& cf, const KronInst<T>* d_inst, int n,
+                              int64_t total, bool use_z, cudaStream_t st) {
+  const size_t smem = kron_smem<T, CH, TL>(use_z, true);
+  if (smem > 227 * 1024) return fe_fail(FE_EINVAL, "tile needs %zu bytes of shared memory", smem);
+  if (total < 1 || total > 0x7fffffffLL) return fe_fail(FE_EINVAL, "batched grid of %lld CTAs", (long long)total);
+  auto kern = kron_batch_kernel<T, CH, TL>;
+  FE_TRY(kron_func_setup(kern, smem));
+  KronCoefT<T> cft = convert_coef<T>(cf);
+  kern<<<(unsigned)total, TL::NTHR, smem, st>>>(cft, d_inst, n); fe_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fe_fail(FE_ECUDA, "batched kron launch: %s", cudaGetErrorString(e));
+  return FE_OK;
+}
+
+template <typename T, int CH, int NCH>
+int64_t kron_batch_plan_dispatch(int p, KronInst<T>* inst, int n) {
+  switch (p) {
+    case 1: return kron_batch_plan_t<T, CH, typename KronTileFor<1, NCH>::type>(inst, n);
+    case 2: return kron_batch_plan_t<T, CH, typename KronTileFor<2, NCH>::type>(inst, n);
+    case 3: return kron_batch_plan_t<T, CH, typename KronTileFor<3, NCH>::type>(inst, n);
+    case 4: return kron_batch_plan_t<T, CH, typename KronTileFor<4, NCH>::type>(inst, n);
+    case 5: return kron_batch_plan_t<T, CH, typename KronTileFor<5, NCH>::type>(inst, n);
+    case 6: return kron_batch_plan_t<T, CH, typename KronTileFor<6, NCH>::type>(inst, n);
+    default: return -1;
+  }
+}
+
+template <typename T, int CH, int NCH>
+fe_status kron_batch_dispatch(const KronCoef& cf, int p, const KronInst<T>* d_inst, int n,
+                              int64_t total, bool use_z, cudaStream_t st) {
+  switch (p) {
+#define FE_BCASE(pp)                                                                      \
+  case pp:                                                                                \
+    return kron_batch_launch_t<T, CH, typename KronTileFor<pp, NCH>::type>(cf, d_inst, n, \
+                                                                          total, use_z, st);
+    FE_BCASE(1) FE_BCASE(2) FE_BCASE(3) FE_BCASE(4) FE_BCASE(5) FE_BCASE(6)
+#undef FE_BCASE
+    default: return fe_fail(FE_EUNSUPPORTED, "p = %d", p);
+  }
+}
+
+template <typename T, int CH, int NCH>
+fe_status kron_dispatch(const KronCoef& cf, const KronGeom& g, const KronIO<T>& io,
+                        cudaStream_t st) {
+  switch (g.p) {
+    case 1: return kron_go<T, CH, typename KronTileFor<1, NCH>::type>(cf, g, io, st);
+    case 2: return kron_go<T, CH, typename KronTileFor<2, NCH>::type>(cf, g, io, st);
+    case 3: return kron_go<T, CH, typename KronTileFor<3, NCH>::type>(cf, g, io, st);
+    case 4: return kron_go<T, CH, typename KronTileFor<4, NCH>::type>(cf, g, io, st);
+    case 5: return kron_go<T, CH, typename KronTileFor<5, NCH>::type>(cf, g, io, st);
+    case 6: return kron_go<T, CH, typename KronTileFor<6, NCH>::type>(cf, g, io, st);
+    default: return fe_fail(FE_EUNSUPPORTED, "p = %d", g.p);
+  }
 }
 
 }  // namespace fe

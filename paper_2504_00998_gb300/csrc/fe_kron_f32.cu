@@ -1,23 +1,20 @@
-// Instantiations of the tensor-product operator kernel: float storage, 4-element chunks.
+// Instantiations of the tensor-product operator kernel: float storage, 4-element chunks,
+// 2 chunk(s) per node in a tile.
 #include "fe_kron.cuh"
 
 namespace fe {
 
-fe_status kron_f32(const KronCoef& cf, const KronGeom& g, const KronIO<float>& io, int nch,
-                  cudaStream_t st) {
-  const int nitems = g.bx * g.p * g.by * g.p * nch;
-  const int ipt = nitems <= 512 ? 1 : (nitems <= 1024 ? 2 : 4);  // at most 512 threads
-  if (nitems > 2048) return fe_fail(FE_EINVAL, "tile of %d items exceeds one CTA", nitems);
-#define FE_K(P_)                                                         \
-  case P_:                                                               \
-    if (ipt == 1) return kron_launch_t<float, P_, 4, 1>(cf, g, io, nch, st); \
-    if (ipt == 2) return kron_launch_t<float, P_, 4, 2>(cf, g, io, nch, st); \
-    return kron_launch_t<float, P_, 4, 4>(cf, g, io, nch, st);
-  switch (g.p) {
-    FE_K(1) FE_K(2) FE_K(3) FE_K(4) FE_K(5) FE_K(6)
-    default: return fe_fail(FE_EUNSUPPORTED, "p = %d", g.p);
-  }
-#undef FE_K
+fe_status kron_f32(const KronCoef& cf, const KronGeom& g, const KronIO<float>& io, cudaStream_t st) {
+  return kron_dispatch<float, 4, 2>(cf, g, io, st);
+}
+
+int64_t kron_batch_plan_f32(int p, KronInst<float>* inst, int n) {
+  return kron_batch_plan_dispatch<float, 4, 2>(p, inst, n);
+}
+
+fe_status kron_batch_f32(const KronCoef& cf, int p, const KronInst<float>* d_inst, int n,
+                         int64_t total_ctas, bool use_z, cudaStream_t st) {
+  return kron_batch_dispatch<float, 4, 2>(cf, p, d_inst, n, total_ctas, use_z, st);
 }
 
 }  // namespace fe

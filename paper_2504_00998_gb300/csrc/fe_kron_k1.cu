@@ -1,23 +1,11 @@
-// Instantiations of the tensor-product operator kernel: double storage, 1-element chunks.
+// Instantiations of the tensor-product operator kernel: double storage, 1-element chunks,
+// 1 chunk(s) per node in a tile.
 #include "fe_kron.cuh"
 
 namespace fe {
 
-fe_status kron_k1(const KronCoef& cf, const KronGeom& g, const KronIO<double>& io, int nch,
-                  cudaStream_t st) {
-  const int nitems = g.bx * g.p * g.by * g.p * nch;
-  const int ipt = nitems <= 512 ? 1 : (nitems <= 1024 ? 2 : 4);  // at most 512 threads
-  if (nitems > 2048) return fe_fail(FE_EINVAL, "tile of %d items exceeds one CTA", nitems);
-#define FE_K(P_)                                                         \
-  case P_:                                                               \
-    if (ipt == 1) return kron_launch_t<double, P_, 1, 1>(cf, g, io, nch, st); \
-    if (ipt == 2) return kron_launch_t<double, P_, 1, 2>(cf, g, io, nch, st); \
-    return kron_launch_t<double, P_, 1, 4>(cf, g, io, nch, st);
-  switch (g.p) {
-    FE_K(1) FE_K(2) FE_K(3) FE_K(4) FE_K(5) FE_K(6)
-    default: return fe_fail(FE_EUNSUPPORTED, "p = %d", g.p);
-  }
-#undef FE_K
+fe_status kron_k1(const KronCoef& cf, const KronGeom& g, const KronIO<double>& io, cudaStream_t st) {
+  return kron_dispatch<double, 1, 1>(cf, g, io, st);
 }
 
 }  // namespace fe

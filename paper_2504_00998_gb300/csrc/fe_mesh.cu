@@ -288,7 +288,7 @@ extern "C" fe_status fe_mesh_destroy(fe_mesh* m) {
   if (!m) return FE_OK;
   cudaSetDevice(m->device);
   cudaStreamSynchronize(m->stream);
-  for (int i = 0; i < 10; ++i) if (m->ws[i]) cudaFree(m->ws[i]);
+  for (int i = 0; i < FE_NWS; ++i) if (m->ws[i]) cudaFree(m->ws[i]);
   if (m->tc_err_pinned) cudaFreeHost(m->tc_err_pinned);
   cudaFree(m->d_veff);
   cudaFree(m->d_veff_f);
@@ -323,6 +323,24 @@ extern "C" fe_status fe_mesh_set_stream(fe_mesh* m, void* stream) {
   if (m->cublas) cublasSetStream(m->cublas, m->stream);
   if (m->cusolver) cusolverDnSetStream(m->cusolver, m->stream);
   return FE_OK;
+}
+
+extern "C" fe_status fe_set_option(fe_mesh* m, int option, int64_t value) {
+  if (!m) return fe_fail(FE_EINVAL, "fe_set_option: null mesh");
+  switch (option) {
+    case FE_OPT_RR_PRODUCTS:
+      if (value != FE_RR_PRODUCTS_F64 && value != FE_RR_PRODUCTS_TC32)
+        return fe_fail(FE_EINVAL, "fe_set_option: bad Rayleigh-Ritz product mode");
+      m->rr_products = (int)value;
+      return FE_OK;
+    case FE_OPT_POISSON_PRECOND:
+      if (value != FE_PRECOND_JACOBI && value != FE_PRECOND_JACOBI_PLANES)
+        return fe_fail(FE_EINVAL, "fe_set_option: bad Poisson preconditioner");
+      m->poisson_precond = (int)value;
+      return FE_OK;
+    default:
+      return fe_fail(FE_EINVAL, "fe_set_option: unknown option %d", option);
+  }
 }
 
 extern "C" fe_status fe_node_coords(const fe_mesh* m, double* xyz) {
@@ -398,7 +416,7 @@ extern "C" fe_status fe_set_atoms(fe_mesh* m, int n, const double* R, const doub
   return fe_fields_build(m);
 }
 
-KronGeom fe_geom(const fe_mesh* m, bool psi, const KronTile& t) {
+KronGeom fe_geom(const fe_mesh* m, bool psi) {
   KronGeom g;
   g.p = m->p;
   g.NX = m->NX;
@@ -406,30 +424,6 @@ KronGeom fe_geom(const fe_mesh* m, bool psi, const KronTile& t) {
   g.nz = m->nz;
   g.gz_lo = psi ? m->gz_lo : 0;
   g.NZs = psi ? m->NZs : m->NZ;
-  g.bx = t.bx;
-  g.by = t.by;
-  g.zseg = t.zseg;
-  g.nbx = (m->nx + t.bx - 1) / t.bx;
-  g.nby = (m->ny + t.by - 1) / t.by;
+  g.bx = g.by = g.zseg = g.nbx = g.nby = 0;   // chosen by the launcher
   return g;
-}
-
-KronTile fe_default_tile(const fe_mesh* m, bool psi, int elem_bytes, int64_t nvec) {
-  KronTile t;
-  t.bx = m->nx >= 2 ? 2 : 1;
-  t.by = m->ny >= 2 ? 2 : 1;
-  // vector chunks of 16 bytes per node: 64 bytes per node in a tile
-  int ch = 16 / elem_bytes;
-  int64_t vt = 4 * ch;
-  if (nvec <= 0) nvec = 1;
-  if (nvec < vt) vt = ((nvec + ch - 1) / ch) * ch;
-  t.nch = (int)(vt / ch);
-  // enough CTAs: split z into segments when the xy x vector grid is small
-  int64_t blocks = (int64_t)((m->nx + t.bx - 1) / t.bx) * ((m->ny + t.by - 1) / t.by) *
-                   ((nvec + vt - 1) / vt);
-  int zseg = m->nz;
-  while (zseg > 2 && blocks * ((m->nz + zseg - 1) / zseg) < 2 * 152) zseg = (zseg + 1) / 2;
-  t.zseg = zseg;
-  (void)psi;
-  return t;
 }

@@ -16,6 +16,7 @@
 // device; a block of iterations is captured once into a CUDA graph and replayed, and the
 // host reads the convergence flag between replays.  The iteration cap bounds the loop.
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "fe_blas.cuh"
@@ -169,7 +170,8 @@ __global__ void k_fin_mean(const double* part, CgState* s, double inv_n) {
 __global__ void k_precond(double* __restrict__ r, double* __restrict__ z,
                           const double* __restrict__ dinv, const unsigned char* __restrict__ mask,
                           const CgState* s, int project, int64_t n, double* __restrict__ part_rz,
-                          double* __restrict__ part_rr) {
+                          double* __restrict__ part_rr, const double* __restrict__ cy,
+                          int64_t plane) {
   __shared__ double sh1[fe::RED_THREADS], sh2[fe::RED_THREADS];
   double mean = project ? s->mean : 0.0;
   double a1 = 0.0, a2 = 0.0;
@@ -177,7 +179,7 @@ __global__ void k_precond(double* __restrict__ r, double* __restrict__ z,
        i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS) {
     double ri = r[i];
     if (project) { ri -= mean; r[i] = ri; }
-    double zi = mask[i] ? 0.0 : dinv[i] * ri;
+    double zi = mask[i] ? 0.0 : dinv[i] * ri + (cy ? cy[i / plane] : 0.0);
     z[i] = zi;
     a1 += ri * zi;
     a2 += ri * ri;
@@ -302,6 +304,96 @@ __global__ void k_vbare(PGeom g, const double* __restrict__ phi, const double* _
   }
 }
 
+// ---- z-plane coarse space ---------------------------------------------------------------
+// Basis: one function per phi plane, the indicator of the plane's free nodes.  R x = plane
+// sums over free nodes; the coarse matrix Ac = R K R^T couples planes that share a cell layer.
+
+// out[gz] = sum of x over the free nodes of plane gz (x == nullptr: the free-node count);
+// one block of RED_THREADS per plane, deterministic order
+__global__ void k_plane_sum(const double* __restrict__ x, const unsigned char* __restrict__ mask,
+                            int64_t plane, double* __restrict__ out) {
+  __shared__ double sh[fe::RED_THREADS];
+  const int64_t base = (int64_t)blockIdx.x * plane;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < plane; i += fe::RED_THREADS) {
+    const int64_t id = base + i;
+    if (!mask[id]) a += x ? x[id] : 1.0;
+  }
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+// v = sum of the coarse basis functions of the planes gz = color (mod period)
+__global__ void k_plane_color(const unsigned char* __restrict__ mask, int64_t plane, int period,
+                              int color, double* __restrict__ v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (!mask[i] && (int)((i / plane) % period) == color) ? 1.0 : 0.0;
+}
+
+constexpr int COARSE_COLS = 64;   // coarse unknowns per block of k_coarse_apply
+
+// y = Ainv (s - mean cnt): Ainv is the symmetric (pseudo-)inverse of the coarse matrix,
+// dense [nz][nz]; block b computes y[64 b, 64 b + 64) with four k-slices per column
+__global__ void k_coarse_apply(const double* __restrict__ sums, const double* __restrict__ cnt,
+                               const double* __restrict__ Ainv, const CgState* st, int project,
+                               int nz, double* __restrict__ y) {
+  extern __shared__ double cb[];                    // b[nz], then partials [4][64]
+  double* part = cb + nz;
+  const double mean = project ? st->mean : 0.0;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) cb[k] = sums[k] - mean * cnt[k];
+  __syncthreads();
+  const int jl = threadIdx.x % COARSE_COLS, ks = threadIdx.x / COARSE_COLS;
+  const int j = blockIdx.x * COARSE_COLS + jl;
+  double a = 0.0;
+  if (j < nz)
+    for (int k = ks; k < nz; k += 4) a += Ainv[(int64_t)k * nz + j] * cb[k];
+  part[ks * COARSE_COLS + jl] = a;
+  __syncthreads();
+  if (ks == 0 && j < nz)
+    y[j] = (part[jl] + part[COARSE_COLS + jl]) + (part[2 * COARSE_COLS + jl] + part[3 * COARSE_COLS + jl]);
+}
+
+// In-place inverse of the SPD matrix A [m][m] (row-major) by Cholesky; false if not SPD.
+bool spd_inverse(std::vector<double>& A, int m) {
+  std::vector<double> L((size_t)m * m, 0.0);
+  for (int j = 0; j < m; ++j) {
+    double d = A[(size_t)j * m + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * m + k] * L[(size_t)j * m + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * m + j] = ljj;
+    for (int i = j + 1; i < m; ++i) {
+      double v = A[(size_t)i * m + j];
+      for (int k = 0; k < j; ++k) v -= L[(size_t)i * m + k] * L[(size_t)j * m + k];
+      L[(size_t)i * m + j] = v / ljj;
+    }
+  }
+  // W = L^-1 (lower triangular), then A^-1 = W^T W
+  std::vector<double> W((size_t)m * m, 0.0);
+  for (int c = 0; c < m; ++c) {
+    W[(size_t)c * m + c] = 1.0 / L[(size_t)c * m + c];
+    for (int i = c + 1; i < m; ++i) {
+      double v = 0.0;
+      for (int k = c; k < i; ++k) v -= L[(size_t)i * m + k] * W[(size_t)k * m + c];
+      W[(size_t)i * m + c] = v / L[(size_t)i * m + i];
+    }
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double v = 0.0;
+      for (int k = i; k < m; ++k) v += W[(size_t)k * m + i] * W[(size_t)k * m + j];
+      A[(size_t)i * m + j] = v;
+      A[(size_t)j * m + i] = v;
+    }
+  return true;
+}
+
 PGeom make_geom(const fe_mesh* m) {
   PGeom g;
   g.NX = m->NX; g.NY = m->NY; g.NZ = m->NZ; g.p = m->p;
@@ -347,6 +439,87 @@ extern "C" fe_status fe_poisson_rhs(fe_mesh* m, const double* rho, double* f, do
 static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisson_bc* bc,
                                   double* phi, double* vbare, fe_solve_info* info,
                                   bool use_graph, const double* f_ext, const double* phic_ext);
+
+static bool same_constraints(const fe_poisson_bc& a, const fe_poisson_bc& b) {
+  if (a.kind != b.kind) return false;
+  if (a.kind == FE_BIAS_CEF) return true;
+  if (a.zA != b.zA || a.zB != b.zB || a.has_patch != b.has_patch) return false;
+  if (!a.has_patch) return true;
+  return std::memcmp(a.patch_lo, b.patch_lo, sizeof a.patch_lo) == 0 &&
+         std::memcmp(a.patch_hi, b.patch_hi, sizeof a.patch_hi) == 0;
+}
+
+// The coarse-space inverse for the constraint set of bc (cached on the mesh): the plane
+// matrix Ac[j][i] = e_j^T K e_i from 2p + 1 operator applications (planes of one colour are
+// 2p + 1 apart, so each plane meets at most one of them), then its inverse on the active
+// planes (planes with free nodes; CEF: the last one is dropped to fix the constant), zero
+// elsewhere.  v and w are n-double scratch vectors.  *Ainv is nullptr when the coarse
+// space is off or its matrix is not numerically SPD.
+static fe_status coarse_setup(fe_mesh* m, const fe_poisson_bc* bc, const unsigned char* mask,
+                              double* v, double* w, const double** Ainv, const double** cnt) {
+  *Ainv = nullptr;
+  *cnt = nullptr;
+  const int nz = m->NZ;
+  if (m->poisson_precond != FE_PRECOND_JACOBI_PLANES || nz > 2048) return FE_OK;
+  const int64_t plane = (int64_t)m->NX * m->NY, n = m->n_phi;
+  void* wsp;
+  FE_TRY(fe_ws(m, WS_PCOARSE, sizeof(double) * ((size_t)nz * nz + 2 * (size_t)nz) + 64, &wsp));
+  double* dA = (double*)wsp;
+  double* dcnt = dA + (size_t)nz * nz;
+  double* dsum = dcnt + nz;
+  if (m->pc_state != 0 && m->pc_nz == nz && same_constraints(m->pc_key, *bc)) {
+    if (m->pc_state == 1) { *Ainv = dA; *cnt = dcnt; }
+    return FE_OK;
+  }
+  cudaStream_t st = m->stream;
+  const int period = 2 * m->p + 1;
+  std::vector<double> wsum((size_t)period * nz), hcnt(nz);
+  k_plane_sum<<<nz, fe::RED_THREADS, 0, st>>>(nullptr, mask, plane, dcnt); fe_count_launch();
+  FE_CUDA(cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(double) * nz, cudaMemcpyDeviceToHost, st));
+  for (int c = 0; c < period; ++c) {
+    k_plane_color<<<fe::grid_for(n), 256, 0, st>>>(mask, plane, period, c, v, n); fe_count_launch();
+    FE_TRY(fe_poisson_apply_K(m, v, w));
+    k_plane_sum<<<nz, fe::RED_THREADS, 0, st>>>(w, mask, plane, dsum); fe_count_launch();
+    FE_CUDA(cudaMemcpyAsync(wsum.data() + (size_t)c * nz, dsum, sizeof(double) * nz,
+                            cudaMemcpyDeviceToHost, st));
+  }
+  FE_CUDA(cudaStreamSynchronize(st));
+  // active planes and the dense coarse matrix on them
+  std::vector<int> act;
+  for (int j = 0; j < nz; ++j) if (hcnt[j] > 0.5) act.push_back(j);
+  if (bc->kind == FE_BIAS_CEF && !act.empty()) act.pop_back();
+  const int na = (int)act.size();
+  std::vector<int> pos(nz, -1);
+  for (int a = 0; a < na; ++a) pos[act[a]] = a;
+  std::vector<double> A((size_t)na * na, 0.0);
+  for (int a = 0; a < na; ++a) {
+    const int j = act[a];
+    for (int i = j - m->p; i <= j + m->p; ++i) {
+      if (i < 0 || i >= nz || pos[i] < 0) continue;
+      A[(size_t)a * na + pos[i]] = wsum[(size_t)(i % period) * nz + j];
+    }
+  }
+  for (int a = 0; a < na; ++a)
+    for (int b = 0; b < a; ++b) {
+      const double s2 = 0.5 * (A[(size_t)a * na + b] + A[(size_t)b * na + a]);
+      A[(size_t)a * na + b] = A[(size_t)b * na + a] = s2;
+    }
+  m->pc_key = *bc;
+  m->pc_nz = nz;
+  if (na == 0 || !spd_inverse(A, na)) {
+    m->pc_state = 2;
+    return FE_OK;
+  }
+  std::vector<double> full((size_t)nz * nz, 0.0);
+  for (int a = 0; a < na; ++a)
+    for (int b = 0; b < na; ++b) full[(size_t)act[a] * nz + act[b]] = A[(size_t)a * na + b];
+  FE_CUDA(cudaMemcpyAsync(dA, full.data(), sizeof(double) * full.size(), cudaMemcpyHostToDevice, st));
+  FE_CUDA(cudaStreamSynchronize(st));
+  m->pc_state = 1;
+  *Ainv = dA;
+  *cnt = dcnt;
+  return FE_OK;
+}
 
 // The solve runs on the mesh's private non-blocking stream (ordered after the caller's stream
 // with an event, and the caller's stream ordered after it), because CUDA graphs cannot be
@@ -422,8 +595,8 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   cudaStream_t st = m->stream;
   // workspace: f, dinv, r, z, p, q (6 n doubles), mask (n bytes), partials, state
   void* wsp;
-  size_t bytes = n * sizeof(double) * 6 + 4 * fe::RED_BLOCKS * sizeof(double) + sizeof(CgState) +
-                 n + 256;
+  size_t bytes = n * sizeof(double) * 6 + 4 * fe::RED_BLOCKS * sizeof(double) +
+                 sizeof(double) * (size_t)m->NZ + sizeof(CgState) + n + 256;
   FE_TRY(fe_ws(m, WS_CG, bytes, &wsp));
   double* f = (double*)wsp;
   double* dinv = f + n;
@@ -435,7 +608,8 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   double* pb = pa + fe::RED_BLOCKS;
   double* pc = pb + fe::RED_BLOCKS;
   double* pd = pc + fe::RED_BLOCKS;
-  CgState* s = (CgState*)(pd + fe::RED_BLOCKS);
+  double* cyv = pd + fe::RED_BLOCKS;
+  CgState* s = (CgState*)(cyv + m->NZ);
   unsigned char* mask = (unsigned char*)(s + 1);
   const int project = bc->kind == FE_BIAS_CEF;
   const double* rh = rho ? rho : m->d_rho;
@@ -453,6 +627,21 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
     k_fin_project_load<<<1, fe::RED_BLOCKS, 0, st>>>(pa, pb, s); fe_count_launch();
     k_project_load<<<gb, 256, 0, st>>>(f, m->d_mass, s, n); fe_count_launch();
   }
+  // coarse space of z-planes (z and q serve as scratch before the iteration starts)
+  const double* Ainv = nullptr;
+  const double* ccnt = nullptr;
+  FE_TRY(coarse_setup(m, bc, mask, z, q, &Ainv, &ccnt));
+  const int nzp = m->NZ;
+  const int64_t plane = (int64_t)m->NX * m->NY;
+  double* csum = Ainv ? (double*)(ccnt + nzp) : nullptr;   // plane sums (scratch)
+  double* cy = Ainv ? cyv : nullptr;                         // coarse correction per plane
+  const int cblocks = (nzp + COARSE_COLS - 1) / COARSE_COLS;
+  const size_t csmem = sizeof(double) * ((size_t)nzp + 4 * COARSE_COLS);
+  auto coarse = [&]() {
+    if (!Ainv) return;
+    k_plane_sum<<<nzp, fe::RED_THREADS, 0, st>>>(r, mask, plane, csum); fe_count_launch();
+    k_coarse_apply<<<cblocks, 4 * COARSE_COLS, csmem, st>>>(csum, ccnt, Ainv, s, project, nzp, cy); fe_count_launch();
+  };
   // r0 = f - K phi0 (phi0 = constrained values, zero elsewhere)
   FE_TRY(fe_poisson_apply_K(m, phi, q));
   k_resid0<<<gb, 256, 0, st>>>(f, q, mask, r, n); fe_count_launch();
@@ -460,7 +649,8 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
     k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, nullptr, n, pa); fe_count_launch();
     k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(pa, s, 1.0 / (double)n); fe_count_launch();
   }
-  k_precond<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, z, dinv, mask, s, project, n, pc, pd); fe_count_launch();
+  coarse();
+  k_precond<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, z, dinv, mask, s, project, n, pc, pd, cy, plane); fe_count_launch();
   k_fin_init<<<1, fe::RED_BLOCKS, 0, st>>>(pc, pd, s, bc->rtol); fe_count_launch();
   k_copy<<<gb, 256, 0, st>>>(z, p, n); fe_count_launch();
   FE_CUDA(cudaGetLastError());
@@ -471,8 +661,9 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
     k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(p, q, n, pa); fe_count_launch();
     k_fin_alpha<<<1, fe::RED_BLOCKS, 0, st>>>(pa, s); fe_count_launch();
     k_update_xr<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(phi, r, p, q, mask, s, n, pb); fe_count_launch();
-    if (project) k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(pb, s, 1.0 / (double)n); fe_count_launch();
-    k_precond<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, z, dinv, mask, s, project, n, pc, pd); fe_count_launch();
+    if (project) { k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(pb, s, 1.0 / (double)n); fe_count_launch(); }
+    coarse();
+    k_precond<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, z, dinv, mask, s, project, n, pc, pd, cy, plane); fe_count_launch();
     k_fin_beta<<<1, fe::RED_BLOCKS, 0, st>>>(pc, pd, s); fe_count_launch();
     k_update_p<<<gb, 256, 0, st>>>(p, z, s, n); fe_count_launch();
     return FE_OK;

@@ -162,19 +162,14 @@ __global__ void k_diag(const double* __restrict__ R, int n, double* __restrict__
     out[j] = R[(int64_t)j * n + j];
 }
 
-// Gram path.  HX is the block Ht X (double, same layout).  X is overwritten by X C into Xout
-// (may equal X only through the temporary tmp).  *ill = true when the caller must fall
-// back to the explicit orthonormalisation.
-fe_status rr_gram_path(fe_mesh* m, const double* X, int64_t ld, const double* HX, int64_t ldh,
-                       int64_t nvec, RrWs& w, double* Xout, int64_t ldo, double* eig, bool* ill) {
+// n x n part of the Gram path.  On entry w.S holds X^T X (upper triangle at least) and w.Q
+// holds X^T Ht X; on exit w.Q holds C = D R^-1 Q and eig the Ritz values, or *ill is set
+// when the scaled Gram matrix is not safely positive definite.
+fe_status rr_small(fe_mesh* m, int64_t nvec, RrWs& w, double* eig, bool* ill) {
   const int n = (int)nvec;
   cudaStream_t st = m->stream;
-  const double one = 1.0, zero = 0.0;
+  const double one = 1.0;
   *ill = false;
-  // S = A A^T (upper), Hs = A B^T
-  FE_CUBLAS(cublasDsyrk(m->cublas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, n, (int)m->n_psi, &one,
-                        X, (int)ld, &zero, w.S, n));
-  FE_TRY(gram(m, X, ld, HX, ldh, nvec, w.Q));
   k_inv_sqrt_diag<<<(n + 255) / 256, 256, 0, st>>>(w.S, n, w.d); fe_count_launch();
   k_fill_lower<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.S, n); fe_count_launch();
   k_scale_sym<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.S, n, w.d); fe_count_launch();
@@ -207,13 +202,71 @@ fe_status rr_gram_path(fe_mesh* m, const double* X, int64_t ld, const double* HX
   FE_CUBLAS(cublasDtrsm(m->cublas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
                         CUBLAS_DIAG_NON_UNIT, n, n, &one, w.S, n, w.Q, n));
   k_scale_rows<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.Q, n, w.d); fe_count_launch();
-  // Xout^T = C^T A
-  FE_CUBLAS(cublasDgemm(m->cublas, CUBLAS_OP_T, CUBLAS_OP_N, n, (int)m->n_psi, n, &one, w.Q, n,
-                        X, (int)ld, &zero, Xout, (int)ldo));
   FE_CUDA(cudaMemcpyAsync(eig, w.eig, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   FE_CUDA(cudaMemcpyAsync(&hinfo, w.info, sizeof(int), cudaMemcpyDeviceToHost, st));
   FE_CUDA(cudaStreamSynchronize(st));
   if (hinfo != 0) return fe_fail(FE_ECUDA, "syevd info %d", hinfo);
+  return FE_OK;
+}
+
+// Gram path with double products.  HX is the block Ht X (double, same layout); Xout <- X C.
+fe_status rr_gram_path(fe_mesh* m, const double* X, int64_t ld, const double* HX, int64_t ldh,
+                       int64_t nvec, RrWs& w, double* Xout, int64_t ldo, double* eig, bool* ill) {
+  const int n = (int)nvec;
+  const double one = 1.0, zero = 0.0;
+  // S = A A^T (upper), Hs = A B^T
+  FE_CUBLAS(cublasDsyrk(m->cublas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, n, (int)m->n_psi, &one,
+                        X, (int)ld, &zero, w.S, n));
+  FE_TRY(gram(m, X, ld, HX, ldh, nvec, w.Q));
+  FE_TRY(rr_small(m, nvec, w, eig, ill));
+  if (*ill) return FE_OK;
+  // Xout^T = C^T A
+  FE_CUBLAS(cublasDgemm(m->cublas, CUBLAS_OP_T, CUBLAS_OP_N, n, (int)m->n_psi, n, &one, w.Q, n,
+                        X, (int)ld, &zero, Xout, (int)ldo));
+  return FE_OK;
+}
+
+__global__ void k_f2d_n(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+__global__ void k_d2f_n(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// Gram path for float storage with the three block products on the tensor cores in cuBLAS's
+// FP32-accurate BF16x9 emulation; the n x n part stays in double.  X <- X C in place.
+fe_status rr_gram_path_tc32(fe_mesh* m, float* X, int64_t ld, const float* HX, int64_t nvec,
+                            RrWs& w, float* tmp, double* eig, bool* ill) {
+  const int n = (int)nvec;
+  const int N = (int)m->n_psi;
+  const float one = 1.0f, zero = 0.0f;
+  void* sp;
+  FE_TRY(fe_ws(m, WS_RR_TC32, sizeof(float) * (size_t)2 * n * n + 64, &sp));
+  float* Sf = (float*)sp;
+  float* Hf = Sf + (size_t)n * n;
+  const cublasComputeType_t ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+  FE_CUBLAS(cublasGemmEx(m->cublas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, N, &one, X, CUDA_R_32F,
+                         (int)ld, X, CUDA_R_32F, (int)ld, &zero, Sf, CUDA_R_32F, n, ct,
+                         CUBLAS_GEMM_DEFAULT));
+  FE_CUBLAS(cublasGemmEx(m->cublas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, N, &one, X, CUDA_R_32F,
+                         (int)ld, HX, CUDA_R_32F, (int)ld, &zero, Hf, CUDA_R_32F, n, ct,
+                         CUBLAS_GEMM_DEFAULT));
+  const int64_t nn = (int64_t)n * n;
+  k_f2d_n<<<fe::grid_for(nn), 256, 0, m->stream>>>(Sf, w.S, nn); fe_count_launch();
+  k_f2d_n<<<fe::grid_for(nn), 256, 0, m->stream>>>(Hf, w.Q, nn); fe_count_launch();
+  FE_TRY(rr_small(m, nvec, w, eig, ill));
+  if (*ill) return FE_OK;
+  k_d2f_n<<<fe::grid_for(nn), 256, 0, m->stream>>>(w.Q, Sf, nn); fe_count_launch();
+  // tmp^T = C^T A
+  FE_CUBLAS(cublasGemmEx(m->cublas, CUBLAS_OP_T, CUBLAS_OP_N, n, N, n, &one, Sf, CUDA_R_32F, n,
+                         X, CUDA_R_32F, (int)ld, &zero, tmp, CUDA_R_32F, (int)ld, ct,
+                         CUBLAS_GEMM_DEFAULT));
+  FE_CUDA(cudaMemcpy2DAsync(X, ld * 4, tmp, ld * 4, nvec * 4, m->n_psi, cudaMemcpyDeviceToDevice,
+                            m->stream));
   return FE_OK;
 }
 
@@ -316,6 +369,18 @@ extern "C" fe_status fe_rayleigh_ritz(fe_mesh* m, void* X, int64_t nvec, int64_t
       return FE_OK;
     }
     return fe_rr_f64(m, Xd, nvec, ld, eig);
+  }
+  if (m->rr_products == 1) {
+    // block products on the tensor cores (FP32-accurate emulation), n x n part in double
+    void* hp;
+    FE_TRY(fe_ws(m, WS_RR_HX, sizeof(float) * (size_t)N * ld * 2, &hp));
+    float* HXf = (float*)hp;
+    float* tmp = HXf + (size_t)N * ld;
+    FE_TRY(fe_hx_step(m, X, HXf, nullptr, nvec, ld, 1.0, 0.0, 0.0, FE_F32));
+    FE_TRY(rr_gram_path_tc32(m, (float*)X, ld, HXf, nvec, w, tmp, eig, &ill));
+    if (!ill) return FE_OK;
+    FE_TRY(fe_ws(m, WS_RR_HX, sizeof(double) * (size_t)N * ld64, &hxp));
+    HX = (double*)hxp;
   }
   // float storage: Ht X in float (sum-factorised), Gram, projection and rotation in double
   void* xp;

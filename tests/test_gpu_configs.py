@@ -87,3 +87,51 @@ def test_p5_slab_sampled_rows(fe):
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol, prec
         del Xg, Y
         torch.cuda.empty_cache()
+
+
+def test_large_lcpd_slab_poisson_and_blocked_filter(fe):
+    """The 48 x 48 x 144 bohr L-CPD slab (24 x 24 x 72 cells, p = 5, 5,198,400 phi nodes,
+    2048 atoms with Z in {1, 3, 4, 5}): the potential satisfies the constraints exactly and
+    the FE equations at sampled free rows (evaluated one by one from the cell definition);
+    the filter runs on one 256-vector block of a 1024-wide array and H X matches the oracle
+    at sampled rows."""
+    slab = W.config5()
+    m = fe.Mesh.from_slab(slab)
+    phi, vbare, info = m.poisson_solve(slab.bias, rtol=1e-10, max_iter=40000)
+    assert info.status == 0 and info.rel_residual <= 1e-10
+    mask, vals = m.poisson_constraints(slab.bias)
+    ph = phi.cpu().numpy()
+    mk = mask.cpu().numpy()
+    assert np.array_equal(ph[mk], vals.cpu().numpy()[mk])
+    # constrained patch: Omega_1 is restricted to the 12 x 12 bohr patch
+    X = m.node_coords().cpu().numpy()
+    top = X[:, 2] >= slab.bias.zB - 1e-12
+    assert 0 < np.sum(mk & top) < np.sum(top)
+    # FE equations K phi = 4 pi M (rho + b) at sampled free rows, from the oracle's cells
+    om = OMesh(slab.L, slab.ncell, slab.p, slab.psi_dirichlet)
+    f, _, _ = m.poisson_rhs()
+    f = f.cpu().numpy()
+    Ke = assembly.reference_cell_stiffness(om)
+    cn = om.cell_nodes()
+    rng = np.random.default_rng(9)
+    free = np.flatnonzero(~mk)
+    rows = rng.choice(free, 30, replace=False)
+    for I in rows:
+        gx, gy, gz = I % om.NX, (I // om.NX) % om.NY, I // (om.NX * om.NY)
+        kphi = sum(Ke[loc] @ ph[cn[cell]] for cell, loc in om.node_cells(gx, gy, gz))
+        assert abs(kphi - f[I]) <= 1e-7 * (np.abs(Ke).max() * np.abs(ph).max() + abs(f[I]))
+    # one 256-vector block of a 1024-wide float array
+    m.set_potential(vbare)
+    Xall = torch.zeros((m.n_psi, 1024), dtype=torch.float32, device="cuda")
+    blk = Xall[:, 256:512]
+    X0 = W.start_block(slab, nvec=256)
+    blk.copy_(torch.from_numpy(X0))
+    Y = torch.zeros_like(Xall)
+    fe._lib.call("fe_apply_H", m.handle, fe._ptr(blk), fe._ptr(Y[:, 256:512]), 256, 1024, fe.FE_F32)
+    V = vbare.cpu().numpy()
+    M = assembly.lumped_mass(om)
+    rows = np.concatenate([[0, om.NX * om.NY, m.n_psi - 1], rng.choice(m.n_psi, 20, replace=False)])
+    ref = assembly.apply_H_rows(om, V, X0, rows, Ke=Ke, M=M)
+    got = Y[torch.tensor(rows, device="cuda"), 256:512].double().cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-5
+    assert torch.all(Y[:, :256] == 0) and torch.all(Y[:, 512:] == 0)

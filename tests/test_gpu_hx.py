@@ -153,3 +153,17 @@ def test_chefsi_converges_to_dense_eigh_on_gpu(fe):
         lam = m.rayleigh_ritz(Xg).cpu().numpy()
         a0 = lam[0]
     np.testing.assert_allclose(lam[:8], ev[:8], atol=1e-10)
+
+
+def test_rayleigh_ritz_tensor_core_products(fe):
+    """Float block with the block products in FP32-accurate tensor-core emulation: Ritz
+    values within the float-storage tolerance of the oracle, orthonormal to 1e-5."""
+    om, H, m, rng = _setup(fe, (4.0, 4.0, 9.0), (2, 2, 4), 3, (True, True), seed=14)
+    m.set_rr_products(True)
+    X = rng.standard_normal((om.n_psi, 12)).astype(np.float32).astype(np.float64)
+    lam_ref, _ = chefsi.rayleigh_ritz(lambda Z: H @ Z, X)
+    Xg = torch.tensor(X, dtype=torch.float32, device="cuda")
+    lam = m.rayleigh_ritz(Xg, prec=fe.FE_F32).cpu().numpy()
+    assert np.max(np.abs(lam - lam_ref)) <= 1e-4
+    Q = Xg.double().cpu().numpy()
+    assert np.max(np.abs(Q.T @ Q - np.eye(12))) <= 1e-5

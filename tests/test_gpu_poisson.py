@@ -123,3 +123,33 @@ def test_iteration_cap_reports_noconv(fe):
     # the mesh stays usable afterwards
     phi, _, info = m.poisson_solve(slab.bias, rtol=1e-10)
     assert info.status == 0
+
+
+@pytest.mark.parametrize("kind", ["cef", "cpd", "lcpd"])
+def test_plane_coarse_space_same_solution_fewer_iterations(fe, kind):
+    """The z-plane coarse correction changes only the iteration count: on a long slab
+    (4 x 4 x 48 bohr, p = 4) both preconditioners reach the oracle's solution, and the
+    two-level one needs clearly fewer iterations."""
+    base = W.small_slab(ncell=(2, 2, 24), p=4, L=(4.0, 4.0, 48.0), natoms=4, seed=13)
+    bias = {"cef": W.Bias("cef", field=0.01),
+            "cpd": W.Bias("cpd", dV=0.05, zA=2.0, zB=46.0),
+            "lcpd": W.Bias("cpd", dV=0.05, zA=2.0, zB=46.0, patch=((1.0, 1.0), (3.0, 3.0)))}[kind]
+    slab = W.Slab(base.name, base.L, base.ncell, base.p, base.R, base.Z, bias)
+    om, K, M, X = _oracle(slab)
+    rho, b = potentials.densities(X, M, slab.R, slab.Z, slab.L)
+    f = 4 * math.pi * M * (rho + b)
+    if kind == "cef":
+        ref = poisson.solve_cef_direct(K, f, M)
+    else:
+        vl = potentials.vloc_minus_vsm(X, slab.R, slab.Z, slab.L)
+        mask, vals, _, _ = potentials.cpd_constraints(X, vl, bias, slab.L)
+        ref = poisson.solve_cpd_direct(K, f, mask, vals)
+    m = fe.Mesh.from_slab(slab)
+    iters = {}
+    for planes in (False, True):
+        m.set_poisson_precond(planes)
+        phi, _, info = m.poisson_solve(bias, rtol=1e-12)
+        assert info.status == 0 and info.rel_residual <= 1e-12
+        assert np.max(np.abs(phi.cpu().numpy() - ref)) <= 1e-9 * np.max(np.abs(ref))
+        iters[planes] = info.iters
+    assert iters[True] < 0.7 * iters[False], iters
