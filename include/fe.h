@@ -94,7 +94,7 @@ fe_status fe_mesh_set_stream(fe_mesh* mesh, void* stream);
  *     FP32-accurate BF16x9 emulation on the float block (relative error ~1e-7, the
  *     precision of the float storage itself); the n x n Cholesky, projection and
  *     eigensolve stay in double.  FE_F64 blocks always use double GEMMs. */
-enum { FE_OPT_RR_PRODUCTS = 0, FE_OPT_POISSON_PRECOND = 1 };
+enum { FE_OPT_RR_PRODUCTS = 0, FE_OPT_POISSON_PRECOND = 1, FE_OPT_POISSON_ARITH = 2 };
 enum { FE_RR_PRODUCTS_F64 = 0, FE_RR_PRODUCTS_TC32 = 1 };
 /*   FE_OPT_POISSON_PRECOND: preconditioner of the Poisson CG.  FE_PRECOND_JACOBI: the
  *     diagonal of K.  FE_PRECOND_JACOBI_PLANES (default): the diagonal plus an exact solve
@@ -105,6 +105,14 @@ enum { FE_RR_PRODUCTS_F64 = 0, FE_RR_PRODUCTS_TC32 = 1 };
  *     which dominate on long slabs.  The converged solution is the same; only the
  *     iteration count changes. */
 enum { FE_PRECOND_JACOBI = 0, FE_PRECOND_JACOBI_PLANES = 1 };
+/*   FE_OPT_POISSON_ARITH: arithmetic of the Poisson solve.  FE_POISSON_F64: CG in double.
+ *     FE_POISSON_MIXED (default): iterative refinement -- the residual f - K phi and the
+ *     update of phi in double, each correction from a float CG (operator, vectors and
+ *     preconditioner in float, dot products accumulated in double) run to a relative
+ *     residual of 1e-4; when a correction stops reducing the double residual, double CG
+ *     finishes from the current phi.  The stopping test (rtol on the double residual) and so
+ *     the accuracy of phi are those of FE_POISSON_F64. */
+enum { FE_POISSON_F64 = 0, FE_POISSON_MIXED = 1 };
 fe_status fe_set_option(fe_mesh* mesh, int option, int64_t value);
 
 /* Node coordinates in phi order, xyz_dev[n_phi][3] (Section 2.3 node layout). */

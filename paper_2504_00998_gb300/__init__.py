@@ -89,6 +89,12 @@ class Mesh:
         call("fe_set_option", self._h, _lib.FE_OPT_POISSON_PRECOND,
              _lib.FE_PRECOND_JACOBI_PLANES if planes else _lib.FE_PRECOND_JACOBI)
 
+    def set_poisson_mixed(self, mixed):
+        """Poisson arithmetic: double CG (False) or float corrections refined against the
+        double residual (True, the default); both stop at the same double residual."""
+        call("fe_set_option", self._h, _lib.FE_OPT_POISSON_ARITH,
+             _lib.FE_POISSON_MIXED if mixed else _lib.FE_POISSON_F64)
+
     def node_coords(self):
         out = self._f64((self.n_phi, 3))
         call("fe_node_coords", self._h, _ptr(out))

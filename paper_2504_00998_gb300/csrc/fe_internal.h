@@ -110,6 +110,9 @@ fe_status kron_f32(const KronCoef& cf, const KronGeom& g, const KronIO<float>& i
                    cudaStream_t st);
 fe_status kron_k1(const KronCoef& cf, const KronGeom& g, const KronIO<double>& io,
                   cudaStream_t st);
+// float with one element per node (the corrections of the mixed-precision Poisson solve)
+fe_status kron_k1f(const KronCoef& cf, const KronGeom& g, const KronIO<float>& io,
+                   cudaStream_t st);
 // Batched launches: plan fills the tile fields, z segmentation, nvt and cta0 of n host
 // instances (g from fe_geom, io.nvec set) and returns the total CTA count; launch runs one
 // operator application over the device copy of those instances.
@@ -162,6 +165,8 @@ struct fe_mesh {
   int rr_products = 0;
   // Poisson CG preconditioner: 0 Jacobi, 1 Jacobi plus the exact z-plane coarse solve
   int poisson_precond = 1;
+  // Poisson arithmetic: 0 double CG, 1 float corrections with double residuals
+  int poisson_arith = 1;
   // cached coarse-space inverse (WS_PCOARSE): valid for the constraint set of pc_key
   int pc_state = 0;          // 0 none, 1 valid, 2 not SPD (Jacobi only for this key)
   int pc_nz = 0;

@@ -34,42 +34,59 @@
 
 namespace fe {
 
+// Device copy of the coefficient tables.  Rows have a stride of 8 entries, 16-byte aligned,
+// so that the compiler can fetch four coefficients per constant load.
+constexpr int KCS = 8;
+
 template <typename T>
 struct KronCoefT {
-  T AyM[FE_MAXN1][FE_MAXN1], AyK[FE_MAXN1][FE_MAXN1];
-  T AxM[FE_MAXN1][FE_MAXN1], AxK[FE_MAXN1][FE_MAXN1];
-  T AzK[FE_MAXN1][FE_MAXN1], AzM[FE_MAXN1][FE_MAXN1];
+  alignas(16) T AyM[FE_MAXN1][KCS];
+  alignas(16) T AyK[FE_MAXN1][KCS];
+  alignas(16) T AxM[FE_MAXN1][KCS];
+  alignas(16) T AxK[FE_MAXN1][KCS];
+  // z tables with the plane's input scale folded in: AzKs[j][k] = AzK[j][k] zin / sqrt(mz_k),
+  // mz_k the z mass factor of an interior plane with local index k (k = 0 and k = p: a plane
+  // shared by two cells); a face plane multiplies its inputs by face_fix first
+  alignas(16) T AzKs[FE_MAXN1][KCS];
+  alignas(16) T AzMs[FE_MAXN1][KCS];
   T sig[FE_MAXN1];
-  T wz[FE_MAXN1];
   // 1/sqrt and sqrt of the z mass factor of a plane by local index (index 0: a plane shared
   // by two cells; *_face: the bottom or top face), so that no plane pays a division
   T rsq[FE_MAXN1], sq[FE_MAXN1];
-  T rsq_face, sq_face;
-  T zin, zout, izout;
+  T rsq_face, sq_face, face_fix;
+  T zout, izout;
   int mass_scale;
 };
 
 template <typename T>
 inline KronCoefT<T> convert_coef(const KronCoef& c) {
-  KronCoefT<T> o;
+  KronCoefT<T> o = {};
+  double rsq[FE_MAXN1];
+  for (int i = 0; i < FE_MAXN1; ++i) {
+    const double mz = i == 0 ? 2.0 * c.wz[0] : c.wz[i];
+    rsq[i] = c.mass_scale ? (mz > 0.0 ? 1.0 / std::sqrt(mz) : 0.0) : 1.0;
+  }
+  int p = 0;   // degree: the last local index with a nonzero GLL weight
+  for (int i = 1; i < FE_MAXN1; ++i)
+    if (c.wz[i] > 0.0) p = i;
   for (int i = 0; i < FE_MAXN1; ++i) {
     for (int j = 0; j < FE_MAXN1; ++j) {
       o.AyM[i][j] = (T)c.AyM[i][j];
       o.AyK[i][j] = (T)c.AyK[i][j];
       o.AxM[i][j] = (T)c.AxM[i][j];
       o.AxK[i][j] = (T)c.AxK[i][j];
-      o.AzK[i][j] = (T)c.AzK[i][j];
-      o.AzM[i][j] = (T)c.AzM[i][j];
+      const double sz = c.zin * rsq[(j == p) ? 0 : j];
+      o.AzKs[i][j] = (T)(c.AzK[i][j] * sz);
+      o.AzMs[i][j] = (T)(c.AzM[i][j] * sz);
     }
     o.sig[i] = (T)c.sig[i];
-    o.wz[i] = (T)c.wz[i];
     const double mz = i == 0 ? 2.0 * c.wz[0] : c.wz[i];
     o.rsq[i] = mz > 0.0 ? (T)(1.0 / std::sqrt(mz)) : T(0);
     o.sq[i] = (T)std::sqrt(mz > 0.0 ? mz : 0.0);
   }
   o.rsq_face = c.wz[0] > 0.0 ? (T)(1.0 / std::sqrt(c.wz[0])) : T(0);
   o.sq_face = (T)std::sqrt(c.wz[0] > 0.0 ? c.wz[0] : 0.0);
-  o.zin = (T)c.zin;
+  o.face_fix = c.mass_scale ? (T)std::sqrt(2.0) : T(1);
   o.zout = (T)c.zout;
   o.izout = (T)(1.0 / c.zout);
   o.mass_scale = c.mass_scale;
@@ -207,6 +224,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
   int it_x[IPT], it_y[IPT], it_ch[IPT];
   bool it_own[IPT];
   int64_t it_node[IPT];     // in-plane node index of the output
+  int64_t it_yo[IPT];       // offset of the item's entries in a plane of Y
   T it_sxy[IPT], it_isxy[IPT];
   C acc[IPT][P + 1];
 #pragma unroll
@@ -221,6 +239,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
     const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
     it_own[i] = valid && (x0 + it_x[i] < g.NX) && (y0 + it_y[i] < g.NY) && (v0 < io.nvec);
     it_node[i] = (x0 + it_x[i]) + (int64_t)g.NX * (y0 + it_y[i]);
+    it_yo[i] = it_node[i] * io.ldy + v0;
     it_sxy[i] = cf.mass_scale ? cf.sig[it_x[i] % P] * cf.sig[it_y[i] % P] : T(1);
     it_isxy[i] = T(1) / it_sxy[i];
 #pragma unroll
@@ -286,10 +305,10 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
     const int zs = gzo - g.gz_lo;
     const T ps = cf.zout * rsq_of(gzo);
     const C* zsrc = Zr + (gzo % TL::ZR) * NZI;
+    T* yplane = io.Y + (int64_t)zs * plane_nodes * io.ldy;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
       if (!it_own[i]) continue;
-      const int64_t nid = (int64_t)zs * plane_nodes + it_node[i];
       const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
       const T sc = io.alpha * ps * it_sxy[i];
       C out;
@@ -300,7 +319,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
 #pragma unroll
         for (int e = 0; e < CH; ++e) out.v[e] = C::fma_t(io.beta, zc.v[e], out.v[e]);
       }
-      T* yp = io.Y + nid * io.ldy + v0;
+      T* yp = yplane + it_yo[i];
       if (v0 + CH <= io.nvec) {
         *reinterpret_cast<C*>(yp) = out;
       } else {
@@ -313,7 +332,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
   // Plane with local index K (compile time, so every coefficient is an immediate operand):
   // the potential term of the plane's own nodes (when pot) and the z contraction of its
   // in-plane results into the layer accumulators.
-  auto plane_z = [&](auto kc, bool pot, T s_in, T inv_ps, const T* vv, const C* st,
+  auto plane_z = [&](auto kc, bool pot, bool face, T inv_ps, const T* vv, const C* st,
                      const C* w1, const C* w2) {
     constexpr int K = decltype(kc)::value;
     if constexpr (K <= P) {
@@ -326,25 +345,28 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
         }
         C a = w1[i], b = w2[i];
 #pragma unroll
-        for (int e = 0; e < CH; ++e) { a.v[e] *= s_in; b.v[e] *= s_in; }
+        if (face) {
+#pragma unroll
+          for (int e = 0; e < CH; ++e) { a.v[e] *= cf.face_fix; b.v[e] *= cf.face_fix; }
+        }
 #pragma unroll
         for (int j = 0; j <= P; ++j) {
-          acc[i][j].fma(cf.AzK[j][K], a);
-          acc[i][j].fma(cf.AzM[j][K], b);
+          acc[i][j].fma(cf.AzKs[j][K], a);
+          acc[i][j].fma(cf.AzMs[j][K], b);
         }
       }
     }
   };
-  auto dispatch_z = [&](int k, bool pot, T s_in, T inv_ps, const T* vv, const C* st,
+  auto dispatch_z = [&](int k, bool pot, bool face, T inv_ps, const T* vv, const C* st,
                         const C* w1, const C* w2) {
     switch (k) {
-      case 0: plane_z(std::integral_constant<int, 0>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
-      case 1: plane_z(std::integral_constant<int, 1>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
-      case 2: plane_z(std::integral_constant<int, 2>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
-      case 3: plane_z(std::integral_constant<int, 3>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
-      case 4: plane_z(std::integral_constant<int, 4>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
-      case 5: plane_z(std::integral_constant<int, 5>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
-      case 6: plane_z(std::integral_constant<int, 6>{}, pot, s_in, inv_ps, vv, st, w1, w2); break;
+      case 0: plane_z(std::integral_constant<int, 0>{}, pot, face, inv_ps, vv, st, w1, w2); break;
+      case 1: plane_z(std::integral_constant<int, 1>{}, pot, face, inv_ps, vv, st, w1, w2); break;
+      case 2: plane_z(std::integral_constant<int, 2>{}, pot, face, inv_ps, vv, st, w1, w2); break;
+      case 3: plane_z(std::integral_constant<int, 3>{}, pot, face, inv_ps, vv, st, w1, w2); break;
+      case 4: plane_z(std::integral_constant<int, 4>{}, pot, face, inv_ps, vv, st, w1, w2); break;
+      case 5: plane_z(std::integral_constant<int, 5>{}, pot, face, inv_ps, vv, st, w1, w2); break;
+      case 6: plane_z(std::integral_constant<int, 6>{}, pot, face, inv_ps, vv, st, w1, w2); break;
       default: break;
     }
   };
@@ -357,6 +379,19 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
       for (int j = 1; j <= P; ++j) acc[i][j].zero();
     }
   };
+
+  // scalar-lane items of the in-plane phases (used when each thread has at most one)
+  constexpr int NL = NCH * CH;
+  int y_ibase = 0, y_obase = 0, x_ibase = 0, x_obase = 0;
+  {
+    const int l = tid % NL, r = tid / NL;
+    const int xh = r % BXH, yb = (r / BXH) * P;
+    y_ibase = (yb * BXH + xh) * NL + l;
+    y_obase = (yb * ARS + xh) * NL + l;
+    const int y = r % BYn, xb = (r / BYn) * P;
+    x_ibase = y * ARS * NL + xb * NL + l;
+    x_obase = (y * WRS + xb) * NL + l;
+  }
 
   // ---- sweep -----------------------------------------------------------------------------
   stage_plane(gbeg);
@@ -380,22 +415,16 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
       // the CTA idle at the following barrier).  NL scalars per node, lane-fastest indexing
       // keeps consecutive threads on consecutive words.
       using S1 = Chunk<T, 1>;
-      constexpr int NL = NCH * CH;
       const S1* sts = reinterpret_cast<const S1*>(st);
       S1* As = reinterpret_cast<S1*>(A);
       S1* Bs = reinterpret_cast<S1*>(B);
       // phase Y: a = AyM U, b = AyK U along y for every halo x
-#pragma unroll 1
-      for (int e = tid; e < TL::NYI * CH; e += NTHR) {
-        const int l = e % NL;
-        const int r = e / NL;
-        const int xh = r % BXH;
-        const int yb = (r / BXH) * P;
+      auto phase_y = [&](int ibase, int obase) {
         S1 own[P + 1], prv[P];
 #pragma unroll
-        for (int kk = 0; kk <= P; ++kk) own[kk] = sts[((yb + P + kk) * BXH + xh) * NL + l];
+        for (int kk = 0; kk <= P; ++kk) own[kk] = sts[ibase + (P + kk) * BXH * NL];
 #pragma unroll
-        for (int kk = 0; kk < P; ++kk) prv[kk] = sts[((yb + kk) * BXH + xh) * NL + l];
+        for (int kk = 0; kk < P; ++kk) prv[kk] = sts[ibase + kk * BXH * NL];
 #pragma unroll
         for (int j = 0; j < P; ++j) {
           S1 a, b;
@@ -415,8 +444,17 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
             a.fma(cf.AyM[P][P], own[0]);
             b.fma(cf.AyK[P][P], own[0]);
           }
-          As[((yb + j) * ARS + xh) * NL + l] = a;
-          Bs[((yb + j) * ARS + xh) * NL + l] = b;
+          As[obase + j * ARS * NL] = a;
+          Bs[obase + j * ARS * NL] = b;
+        }
+      };
+      if constexpr (TL::NYI * CH <= NTHR) {
+        if (tid < TL::NYI * CH) phase_y(y_ibase, y_obase);
+      } else {
+#pragma unroll 1
+        for (int e = tid; e < TL::NYI * CH; e += NTHR) {
+          const int l = e % NL, r = e / NL, xh = r % BXH, yb = (r / BXH) * P;
+          phase_y((yb * BXH + xh) * NL + l, (yb * ARS + xh) * NL + l);
         }
       }
       __syncthreads();
@@ -424,19 +462,14 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
       {
         S1* W1s = reinterpret_cast<S1*>(W1);
         S1* W2s = reinterpret_cast<S1*>(W2);
-#pragma unroll 1
-        for (int e = tid; e < TL::NXI * CH; e += NTHR) {
-          const int l = e % NL;
-          const int r = e / NL;
-          const int y = r % BYn;
-          const int xb = (r / BYn) * P;
-          const S1* arow = As + y * ARS * NL;
-          const S1* brow = Bs + y * ARS * NL;
+        auto phase_x = [&](int ibase, int obase) {
+          const S1* arow = As + ibase;
+          const S1* brow = Bs + ibase;
           S1 ao[P + 1], bo[P + 1];
 #pragma unroll
           for (int kk = 0; kk <= P; ++kk) {
-            ao[kk] = arow[(xb + P + kk) * NL + l];
-            bo[kk] = brow[(xb + P + kk) * NL + l];
+            ao[kk] = arow[(P + kk) * NL];
+            bo[kk] = brow[(P + kk) * NL];
           }
 #pragma unroll
           for (int j = 0; j < P; ++j) {
@@ -452,8 +485,8 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
             if (j == 0) {
 #pragma unroll
               for (int kk = 0; kk < P; ++kk) {
-                const S1 ap = arow[(xb + kk) * NL + l];
-                const S1 bp = brow[(xb + kk) * NL + l];
+                const S1 ap = arow[kk * NL];
+                const S1 bp = brow[kk * NL];
                 u.fma(cf.AxM[P][kk], ap);
                 v.fma(cf.AxK[P][kk], ap);
                 v.fma(cf.AxM[P][kk], bp);
@@ -462,8 +495,17 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
               v.fma(cf.AxK[P][P], ao[0]);
               v.fma(cf.AxM[P][P], bo[0]);
             }
-            W1s[(y * WRS + xb + j) * NL + l] = u;
-            W2s[(y * WRS + xb + j) * NL + l] = v;
+            W1s[obase + j * NL] = u;
+            W2s[obase + j * NL] = v;
+          }
+        };
+        if constexpr (TL::NXI * CH <= NTHR) {
+          if (tid < TL::NXI * CH) phase_x(x_ibase, x_obase);
+        } else {
+#pragma unroll 1
+          for (int e = tid; e < TL::NXI * CH; e += NTHR) {
+            const int l = e % NL, r = e / NL, y = r % BYn, xb = (r / BYn) * P;
+            phase_x(y * ARS * NL + xb * NL + l, (y * WRS + xb) * NL + l);
           }
         }
       }
@@ -475,10 +517,10 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
         w1[i] = W1[item];
         w2[i] = W2[item];
       }
-      const T s_in = cf.zin * rsq_of(gz);
+      const bool face = gz == 0 || gz == g.nz * P;
       const T inv_ps = sq_of(gz) * cf.izout;
       const T* vv = Vs + ((gz - gbeg) % TL::NSB) * (BXn * BYn);
-      dispatch_z(k, use_v, s_in, inv_ps, vv, st, w1, w2);
+      dispatch_z(k, use_v, face, inv_ps, vv, st, w1, w2);
       if (k == P) {
         // the layer is complete: its first P planes are final; the top plane's sum
         // becomes the bottom accumulator of the next layer
@@ -486,7 +528,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
         for (int j = 0; j < P; ++j) write_plane(c * P + j, j);
         shift_layer();
         ++c;
-        if (c < c1) dispatch_z(0, false, s_in, inv_ps, vv, st, w1, w2);
+        if (c < c1) dispatch_z(0, false, face, inv_ps, vv, st, w1, w2);
       }
     } else if (k == P) {
       // an unstored (homogeneous Dirichlet) plane contributes nothing
@@ -587,10 +629,13 @@ struct KronBlock {
   static constexpr int B = P == 1 ? 8 : P == 2 ? 5 : P == 3 ? 3 : 2;
 };
 
-template <int P, int NCH>
+// threads: enough for one output item (node, chunk) and one y-phase scalar item each
+template <int P, int NCH, int CH>
 struct KronTileFor {
   static constexpr int B = KronBlock<P>::B;
-  static constexpr int N = B * P * B * P * NCH;
+  static constexpr int NZ_ITEMS = B * P * B * P * NCH;
+  static constexpr int NY_ITEMS = (B * P + P + 1) * B * NCH * CH;
+  static constexpr int N = NZ_ITEMS > NY_ITEMS ? NZ_ITEMS : NY_ITEMS;
   static constexpr int NTHR = (N + 31) / 32 * 32 > 512 ? 512 : (N + 31) / 32 * 32;
   using type = KronTileT<P, B, B, NCH, NTHR>;
 };
@@ -680,12 +725,12 @@ fe_status kron_batch_launch_t(const KronCoef& cf, const KronInst<T>* d_inst, int
 template <typename T, int CH, int NCH>
 int64_t kron_batch_plan_dispatch(int p, KronInst<T>* inst, int n) {
   switch (p) {
-    case 1: return kron_batch_plan_t<T, CH, typename KronTileFor<1, NCH>::type>(inst, n);
-    case 2: return kron_batch_plan_t<T, CH, typename KronTileFor<2, NCH>::type>(inst, n);
-    case 3: return kron_batch_plan_t<T, CH, typename KronTileFor<3, NCH>::type>(inst, n);
-    case 4: return kron_batch_plan_t<T, CH, typename KronTileFor<4, NCH>::type>(inst, n);
-    case 5: return kron_batch_plan_t<T, CH, typename KronTileFor<5, NCH>::type>(inst, n);
-    case 6: return kron_batch_plan_t<T, CH, typename KronTileFor<6, NCH>::type>(inst, n);
+    case 1: return kron_batch_plan_t<T, CH, typename KronTileFor<1, NCH, CH>::type>(inst, n);
+    case 2: return kron_batch_plan_t<T, CH, typename KronTileFor<2, NCH, CH>::type>(inst, n);
+    case 3: return kron_batch_plan_t<T, CH, typename KronTileFor<3, NCH, CH>::type>(inst, n);
+    case 4: return kron_batch_plan_t<T, CH, typename KronTileFor<4, NCH, CH>::type>(inst, n);
+    case 5: return kron_batch_plan_t<T, CH, typename KronTileFor<5, NCH, CH>::type>(inst, n);
+    case 6: return kron_batch_plan_t<T, CH, typename KronTileFor<6, NCH, CH>::type>(inst, n);
     default: return -1;
   }
 }
@@ -696,7 +741,7 @@ fe_status kron_batch_dispatch(const KronCoef& cf, int p, const KronInst<T>* d_in
   switch (p) {
 #define FE_BCASE(pp)                                                                      \
   case pp:                                                                                \
-    return kron_batch_launch_t<T, CH, typename KronTileFor<pp, NCH>::type>(cf, d_inst, n, \
+    return kron_batch_launch_t<T, CH, typename KronTileFor<pp, NCH, CH>::type>(cf, d_inst, n, \
                                                                           total, use_z, st);
     FE_BCASE(1) FE_BCASE(2) FE_BCASE(3) FE_BCASE(4) FE_BCASE(5) FE_BCASE(6)
 #undef FE_BCASE
@@ -708,12 +753,12 @@ template <typename T, int CH, int NCH>
 fe_status kron_dispatch(const KronCoef& cf, const KronGeom& g, const KronIO<T>& io,
                         cudaStream_t st) {
   switch (g.p) {
-    case 1: return kron_go<T, CH, typename KronTileFor<1, NCH>::type>(cf, g, io, st);
-    case 2: return kron_go<T, CH, typename KronTileFor<2, NCH>::type>(cf, g, io, st);
-    case 3: return kron_go<T, CH, typename KronTileFor<3, NCH>::type>(cf, g, io, st);
-    case 4: return kron_go<T, CH, typename KronTileFor<4, NCH>::type>(cf, g, io, st);
-    case 5: return kron_go<T, CH, typename KronTileFor<5, NCH>::type>(cf, g, io, st);
-    case 6: return kron_go<T, CH, typename KronTileFor<6, NCH>::type>(cf, g, io, st);
+    case 1: return kron_go<T, CH, typename KronTileFor<1, NCH, CH>::type>(cf, g, io, st);
+    case 2: return kron_go<T, CH, typename KronTileFor<2, NCH, CH>::type>(cf, g, io, st);
+    case 3: return kron_go<T, CH, typename KronTileFor<3, NCH, CH>::type>(cf, g, io, st);
+    case 4: return kron_go<T, CH, typename KronTileFor<4, NCH, CH>::type>(cf, g, io, st);
+    case 5: return kron_go<T, CH, typename KronTileFor<5, NCH, CH>::type>(cf, g, io, st);
+    case 6: return kron_go<T, CH, typename KronTileFor<6, NCH, CH>::type>(cf, g, io, st);
     default: return fe_fail(FE_EUNSUPPORTED, "p = %d", g.p);
   }
 }

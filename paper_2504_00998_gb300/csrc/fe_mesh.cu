@@ -338,6 +338,11 @@ extern "C" fe_status fe_set_option(fe_mesh* m, int option, int64_t value) {
         return fe_fail(FE_EINVAL, "fe_set_option: bad Poisson preconditioner");
       m->poisson_precond = (int)value;
       return FE_OK;
+    case FE_OPT_POISSON_ARITH:
+      if (value != FE_POISSON_F64 && value != FE_POISSON_MIXED)
+        return fe_fail(FE_EINVAL, "fe_set_option: bad Poisson arithmetic");
+      m->poisson_arith = (int)value;
+      return FE_OK;
     default:
       return fe_fail(FE_EINVAL, "fe_set_option: unknown option %d", option);
   }

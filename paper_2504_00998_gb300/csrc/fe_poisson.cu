@@ -15,6 +15,7 @@
 // Every CG iteration is a fixed sequence of stream-ordered launches with all scalars on the
 // device; a block of iterations is captured once into a CUDA graph and replayed, and the
 // host reads the convergence flag between replays.  The iteration cap bounds the loop.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -106,14 +107,15 @@ __global__ void k_setup(PGeom g, fe_poisson_bc bc, const double* __restrict__ ma
   }
 }
 
-// partial sums of x (y == nullptr) or x.y; one partial per block
-__global__ void k_psum(const double* __restrict__ x, const double* __restrict__ y, int64_t n,
+// partial sums of x (y == nullptr) or x.y, accumulated in double; one partial per block
+template <typename V>
+__global__ void k_psum(const V* __restrict__ x, const V* __restrict__ y, int64_t n,
                        double* __restrict__ part) {
   __shared__ double sh[fe::RED_THREADS];
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
        i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS)
-    s += y ? x[i] * y[i] : x[i];
+    s += y ? (double)x[i] * (double)y[i] : (double)x[i];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
@@ -166,23 +168,24 @@ __global__ void k_fin_mean(const double* part, CgState* s, double inv_n) {
   if (threadIdx.x == 0) s->mean = v * inv_n;
 }
 
-// r -= mean (CEF only); z = Dinv r on free rows; one partial of r.z and r.r per block
-__global__ void k_precond(double* __restrict__ r, double* __restrict__ z,
-                          const double* __restrict__ dinv, const unsigned char* __restrict__ mask,
-                          const CgState* s, int project, int64_t n, double* __restrict__ part_rz,
-                          double* __restrict__ part_rr, const double* __restrict__ cy,
-                          int64_t plane) {
+// r -= mean (CEF only); z = Dinv r (+ the coarse correction of the node's plane) on free
+// rows; one partial of r.z and r.r per block (of the stored, possibly rounded, values)
+template <typename V>
+__global__ void k_precond(V* __restrict__ r, V* __restrict__ z, const V* __restrict__ dinv,
+                          const unsigned char* __restrict__ mask, const CgState* s, int project,
+                          int64_t n, double* __restrict__ part_rz, double* __restrict__ part_rr,
+                          const double* __restrict__ cy, int64_t plane) {
   __shared__ double sh1[fe::RED_THREADS], sh2[fe::RED_THREADS];
-  double mean = project ? s->mean : 0.0;
+  const double mean = project ? s->mean : 0.0;
   double a1 = 0.0, a2 = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
        i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS) {
-    double ri = r[i];
-    if (project) { ri -= mean; r[i] = ri; }
-    double zi = mask[i] ? 0.0 : dinv[i] * ri + (cy ? cy[i / plane] : 0.0);
+    V ri = r[i];
+    if (project) { ri = (V)((double)ri - mean); r[i] = ri; }
+    const V zi = mask[i] ? V(0) : (V)((double)dinv[i] * (double)ri + (cy ? cy[i / plane] : 0.0));
     z[i] = zi;
-    a1 += ri * zi;
-    a2 += ri * ri;
+    a1 += (double)ri * (double)zi;
+    a2 += (double)ri * (double)ri;
   }
   sh1[threadIdx.x] = a1;
   sh2[threadIdx.x] = a2;
@@ -195,20 +198,23 @@ __global__ void k_precond(double* __restrict__ r, double* __restrict__ z,
 }
 
 // first iteration: p = z, rz, rr, |b|^2
-__global__ void k_fin_init(const double* part_rz, const double* part_rr, CgState* s, double rtol) {
+// (tol2_abs > 0: that absolute bound on |r|^2, else rtol relative to this initial residual)
+__global__ void k_fin_init(const double* part_rz, const double* part_rr, CgState* s, double rtol,
+                           double tol2_abs) {
   double rz = block_sum_partials(part_rz);
   double rr = block_sum_partials(part_rr);
   if (threadIdx.x == 0) {
     s->rz = rz;
     s->rr = rr;
     s->bnorm2 = rr;
-    s->tol2 = rtol * rtol * rr;
+    s->tol2 = tol2_abs > 0.0 ? tol2_abs : rtol * rtol * rr;
     s->done = (rr <= s->tol2) || rr == 0.0;
     s->iters = 0;
   }
 }
 
-__global__ void k_copy(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+template <typename V>
+__global__ void k_copy(const V* __restrict__ a, V* __restrict__ b, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     b[i] = a[i];
@@ -224,22 +230,22 @@ __global__ void k_fin_alpha(const double* part, CgState* s) {
 }
 
 // x += alpha p; r -= alpha q (free rows); partial sums of r for the projection
-__global__ void k_update_xr(double* __restrict__ x, double* __restrict__ r,
-                            const double* __restrict__ p, const double* __restrict__ q,
-                            const unsigned char* __restrict__ mask, const CgState* s, int64_t n,
-                            double* __restrict__ part) {
+template <typename V>
+__global__ void k_update_xr(V* __restrict__ x, V* __restrict__ r, const V* __restrict__ p,
+                            const V* __restrict__ q, const unsigned char* __restrict__ mask,
+                            const CgState* s, int64_t n, double* __restrict__ part) {
   __shared__ double sh[fe::RED_THREADS];
-  double a = s->alpha;
+  const double a = s->alpha;
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
        i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS) {
-    double ri = r[i];
+    V ri = r[i];
     if (!mask[i]) {
-      x[i] += a * p[i];
-      ri -= a * q[i];
+      x[i] = (V)((double)x[i] + a * (double)p[i]);
+      ri = (V)((double)ri - a * (double)q[i]);
       r[i] = ri;
     }
-    acc += ri;
+    acc += (double)ri;
   }
   sh[threadIdx.x] = acc;
   __syncthreads();
@@ -268,13 +274,38 @@ __global__ void k_fin_beta(const double* part_rz, const double* part_rr, CgState
 }
 
 // p = z + beta p (skipped once converged so p, x stay fixed)
-__global__ void k_update_p(double* __restrict__ p, const double* __restrict__ z, const CgState* s,
+template <typename V>
+__global__ void k_update_p(V* __restrict__ p, const V* __restrict__ z, const CgState* s,
                            int64_t n) {
   if (s->done && s->alpha == 0.0) return;
-  double b = s->beta;
+  const double b = s->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + b * p[i];
+    p[i] = (V)((double)z[i] + b * (double)p[i]);
+}
+
+// mixed-precision refinement: the float copy of the double residual, and phi += delta
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void k_add_delta(double* __restrict__ phi, const float* __restrict__ d,
+                            const unsigned char* __restrict__ mask, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!mask[i]) phi[i] += (double)d[i];
+}
+// r -= mean (after k_fin_mean); |r|^2 goes through k_psum
+__global__ void k_sub_mean(double* __restrict__ r, const CgState* s, int64_t n) {
+  const double c = s->mean;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    r[i] -= c;
+}
+__global__ void k_fin_rr(const double* part, CgState* s) {
+  double v = block_sum_partials(part);
+  if (threadIdx.x == 0) s->rr = v;
 }
 
 // CEF: phi -= (M . phi) / sum M
@@ -310,14 +341,15 @@ __global__ void k_vbare(PGeom g, const double* __restrict__ phi, const double* _
 
 // out[gz] = sum of x over the free nodes of plane gz (x == nullptr: the free-node count);
 // one block of RED_THREADS per plane, deterministic order
-__global__ void k_plane_sum(const double* __restrict__ x, const unsigned char* __restrict__ mask,
+template <typename V>
+__global__ void k_plane_sum(const V* __restrict__ x, const unsigned char* __restrict__ mask,
                             int64_t plane, double* __restrict__ out) {
   __shared__ double sh[fe::RED_THREADS];
   const int64_t base = (int64_t)blockIdx.x * plane;
   double a = 0.0;
   for (int64_t i = threadIdx.x; i < plane; i += fe::RED_THREADS) {
     const int64_t id = base + i;
-    if (!mask[id]) a += x ? x[id] : 1.0;
+    if (!mask[id]) a += x ? (double)x[id] : 1.0;
   }
   sh[threadIdx.x] = a;
   __syncthreads();
@@ -474,7 +506,7 @@ static fe_status coarse_setup(fe_mesh* m, const fe_poisson_bc* bc, const unsigne
   cudaStream_t st = m->stream;
   const int period = 2 * m->p + 1;
   std::vector<double> wsum((size_t)period * nz), hcnt(nz);
-  k_plane_sum<<<nz, fe::RED_THREADS, 0, st>>>(nullptr, mask, plane, dcnt); fe_count_launch();
+  k_plane_sum<double><<<nz, fe::RED_THREADS, 0, st>>>(nullptr, mask, plane, dcnt); fe_count_launch();
   FE_CUDA(cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(double) * nz, cudaMemcpyDeviceToHost, st));
   for (int c = 0; c < period; ++c) {
     k_plane_color<<<fe::grid_for(n), 256, 0, st>>>(mask, plane, period, c, v, n); fe_count_launch();
@@ -579,6 +611,127 @@ extern "C" fe_status fe_poisson_solve_load(fe_mesh* m, const double* f, const fe
   return poisson_solve_forked(m, nullptr, bc, phi, nullptr, info, f, phic);
 }
 
+// ---- preconditioned CG in a given vector precision -------------------------------------------
+namespace {
+
+template <typename V>
+struct CgBuf {
+  V *x, *r, *z, *p, *q;
+  const V* dinv;
+  const unsigned char* mask;
+  double *pa, *pb, *pc, *pd;   // block partials
+  CgState* s;
+  const double* Ainv;          // coarse space (nullptr: Jacobi only)
+  const double* ccnt;
+  double* csum;
+  double* cy;
+};
+
+fe_status apply_K_v(fe_mesh* m, const double* x, double* y) { return fe_poisson_apply_K(m, x, y); }
+fe_status apply_K_v(fe_mesh* m, const float* x, float* y) {
+  KronIO<float> io{x, 1, y, 1, nullptr, 1, nullptr, 1, 1.0f, 0.0f, 0.0f};
+  return fe::kron_k1f(m->coefK, fe_geom(m, false), io, m->stream);
+}
+
+// CG on K_ff x = r0 from the iterate in b.x, whose masked residual is in b.r (projected by
+// the first preconditioner call for CEF).  Stops at |r|^2 <= tol2_abs, or (tol2_abs <= 0)
+// |r|^2 <= rtol^2 |r0|^2, or after maxit iterations.  Blocks of iterations replay a CUDA graph
+// captured on first use (*exec, kept by the caller for the rest of the solve).
+template <typename V>
+fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double tol2_abs,
+                 int maxit, bool use_graph, cudaGraphExec_t* exec, int64_t* graph_kernels,
+                 CgState* out) {
+  const int64_t n = m->n_phi;
+  const int64_t plane = (int64_t)m->NX * m->NY;
+  const int nzp = m->NZ;
+  cudaStream_t st = m->stream;
+  const int gb = fe::grid_for(n);
+  const int cblocks = (nzp + COARSE_COLS - 1) / COARSE_COLS;
+  const size_t csmem = sizeof(double) * ((size_t)nzp + 4 * COARSE_COLS);
+  auto coarse = [&]() {
+    if (!b.Ainv) return;
+    k_plane_sum<V><<<nzp, fe::RED_THREADS, 0, st>>>(b.r, b.mask, plane, b.csum); fe_count_launch();
+    k_coarse_apply<<<cblocks, 4 * COARSE_COLS, csmem, st>>>(b.csum, b.ccnt, b.Ainv, b.s, project,
+                                                            nzp, b.cy); fe_count_launch();
+  };
+  const double* cy = b.Ainv ? b.cy : nullptr;
+  CgState s0 = {};
+  s0.maxit = maxit;
+  FE_CUDA(cudaMemcpyAsync(b.s, &s0, sizeof(CgState), cudaMemcpyHostToDevice, st));
+  if (project) {
+    k_psum<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, nullptr, n, b.pa); fe_count_launch();
+    k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(b.pa, b.s, 1.0 / (double)n); fe_count_launch();
+  }
+  coarse();
+  k_precond<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project, n,
+                                                           b.pc, b.pd, cy, plane); fe_count_launch();
+  k_fin_init<<<1, fe::RED_BLOCKS, 0, st>>>(b.pc, b.pd, b.s, rtol, tol2_abs); fe_count_launch();
+  k_copy<V><<<gb, 256, 0, st>>>(b.z, b.p, n); fe_count_launch();
+  FE_CUDA(cudaGetLastError());
+
+  auto iteration = [&]() -> fe_status {
+    FE_TRY(apply_K_v(m, b.p, b.q));
+    k_psum<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.p, b.q, n, b.pa); fe_count_launch();
+    k_fin_alpha<<<1, fe::RED_BLOCKS, 0, st>>>(b.pa, b.s); fe_count_launch();
+    k_update_xr<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.x, b.r, b.p, b.q, b.mask, b.s, n,
+                                                               b.pb); fe_count_launch();
+    if (project) { k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(b.pb, b.s, 1.0 / (double)n); fe_count_launch(); }
+    coarse();
+    k_precond<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project,
+                                                             n, b.pc, b.pd, cy, plane); fe_count_launch();
+    k_fin_beta<<<1, fe::RED_BLOCKS, 0, st>>>(b.pc, b.pd, b.s); fe_count_launch();
+    k_update_p<V><<<gb, 256, 0, st>>>(b.p, b.z, b.s, n); fe_count_launch();
+    return FE_OK;
+  };
+  const int per_graph = 16;
+  if (use_graph && !*exec) {
+    cudaGraph_t graph = nullptr;
+    FE_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    fe_status cst = FE_OK;
+    const int64_t before = fe_kernel_launches();
+    for (int i = 0; i < per_graph && cst == FE_OK; ++i) cst = iteration();
+    // captured launches run only when the graph is replayed
+    *graph_kernels = fe_kernel_launches() - before;
+    fe_count_launch(-*graph_kernels);
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (cst != FE_OK) { cudaGetLastError(); if (graph) cudaGraphDestroy(graph); return cst; }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fe_fail(FE_ECUDA, "CG capture: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *exec = nullptr;
+      return fe_fail(FE_ECUDA, "CG graph: %s", cudaGetErrorString(e));
+    }
+  }
+  int launched = 0;
+  while (true) {
+    FE_CUDA(cudaMemcpyAsync(out, b.s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaStreamSynchronize(st));
+    if (out->done || launched >= maxit) break;
+    if (use_graph) {
+      cudaError_t e = cudaGraphLaunch(*exec, st);
+      if (e != cudaSuccess) return fe_fail(FE_ECUDA, "CG graph launch: %s", cudaGetErrorString(e));
+      fe_count_launch(*graph_kernels);
+      launched += per_graph;
+    } else {
+      FE_TRY(iteration());
+      launched += 1;
+    }
+  }
+  return FE_OK;
+}
+
+struct GraphExec {
+  cudaGraphExec_t e = nullptr;
+  ~GraphExec() { if (e) cudaGraphExecDestroy(e); }
+};
+
+}  // namespace
+
 static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisson_bc* bc,
                                   double* phi, double* vbare, fe_solve_info* info,
                                   bool use_graph, const double* f_ext, const double* phic_ext) {
@@ -592,11 +745,15 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
     return fe_fail(FE_EINVAL, "fe_poisson_solve: need zA < zB");
   FE_TRY(fe_activate(m));
   const int64_t n = m->n_phi;
+  const int nzp = m->NZ;
   cudaStream_t st = m->stream;
-  // workspace: f, dinv, r, z, p, q (6 n doubles), mask (n bytes), partials, state
+  const bool mixed = m->poisson_arith == FE_POISSON_MIXED;
+  // workspace: double f, dinv, r, z, p, q; float r, z, p, q, delta, dinv (mixed only);
+  // partials, coarse correction, two states, mask
   void* wsp;
-  size_t bytes = n * sizeof(double) * 6 + 4 * fe::RED_BLOCKS * sizeof(double) +
-                 sizeof(double) * (size_t)m->NZ + sizeof(CgState) + n + 256;
+  const size_t nd = (size_t)n * 6, nf = mixed ? (size_t)n * 6 : 0;
+  size_t bytes = nd * sizeof(double) + nf * sizeof(float) + 64 +
+                 (4 * fe::RED_BLOCKS + (size_t)nzp) * sizeof(double) + 2 * sizeof(CgState) + n + 256;
   FE_TRY(fe_ws(m, WS_CG, bytes, &wsp));
   double* f = (double*)wsp;
   double* dinv = f + n;
@@ -604,26 +761,25 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   double* z = r + n;
   double* p = z + n;
   double* q = p + n;
-  double* pa = q + n;
+  float* fl = (float*)(q + n);
+  double* pa = (double*)(((uintptr_t)(fl + nf) + 63) & ~(uintptr_t)63);
   double* pb = pa + fe::RED_BLOCKS;
   double* pc = pb + fe::RED_BLOCKS;
   double* pd = pc + fe::RED_BLOCKS;
   double* cyv = pd + fe::RED_BLOCKS;
-  CgState* s = (CgState*)(cyv + m->NZ);
-  unsigned char* mask = (unsigned char*)(s + 1);
+  CgState* s = (CgState*)(cyv + nzp);
+  CgState* sref = s + 1;
+  unsigned char* mask = (unsigned char*)(sref + 1);
   const int project = bc->kind == FE_BIAS_CEF;
   const double* rh = rho ? rho : m->d_rho;
   const int gb = fe::grid_for(n);
   PGeom g = make_geom(m);
 
-  CgState s0 = {};
-  s0.maxit = bc->max_iter;
-  FE_CUDA(cudaMemcpyAsync(s, &s0, sizeof(CgState), cudaMemcpyHostToDevice, st));
   k_setup<<<gb, 256, 0, st>>>(g, *bc, m->d_mass, rh, m->d_b, m->d_vlms, f_ext, phic_ext, f, dinv,
                               mask, phi, n); fe_count_launch();
   if (project) {
-    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(f, nullptr, n, pa); fe_count_launch();
-    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(m->d_mass, nullptr, n, pb); fe_count_launch();
+    k_psum<double><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(f, nullptr, n, pa); fe_count_launch();
+    k_psum<double><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(m->d_mass, nullptr, n, pb); fe_count_launch();
     k_fin_project_load<<<1, fe::RED_BLOCKS, 0, st>>>(pa, pb, s); fe_count_launch();
     k_project_load<<<gb, 256, 0, st>>>(f, m->d_mass, s, n); fe_count_launch();
   }
@@ -631,92 +787,75 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   const double* Ainv = nullptr;
   const double* ccnt = nullptr;
   FE_TRY(coarse_setup(m, bc, mask, z, q, &Ainv, &ccnt));
-  const int nzp = m->NZ;
-  const int64_t plane = (int64_t)m->NX * m->NY;
-  double* csum = Ainv ? (double*)(ccnt + nzp) : nullptr;   // plane sums (scratch)
-  double* cy = Ainv ? cyv : nullptr;                         // coarse correction per plane
-  const int cblocks = (nzp + COARSE_COLS - 1) / COARSE_COLS;
-  const size_t csmem = sizeof(double) * ((size_t)nzp + 4 * COARSE_COLS);
-  auto coarse = [&]() {
-    if (!Ainv) return;
-    k_plane_sum<<<nzp, fe::RED_THREADS, 0, st>>>(r, mask, plane, csum); fe_count_launch();
-    k_coarse_apply<<<cblocks, 4 * COARSE_COLS, csmem, st>>>(csum, ccnt, Ainv, s, project, nzp, cy); fe_count_launch();
-  };
-  // r0 = f - K phi0 (phi0 = constrained values, zero elsewhere)
-  FE_TRY(fe_poisson_apply_K(m, phi, q));
-  k_resid0<<<gb, 256, 0, st>>>(f, q, mask, r, n); fe_count_launch();
-  if (project) {
-    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, nullptr, n, pa); fe_count_launch();
-    k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(pa, s, 1.0 / (double)n); fe_count_launch();
-  }
-  coarse();
-  k_precond<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, z, dinv, mask, s, project, n, pc, pd, cy, plane); fe_count_launch();
-  k_fin_init<<<1, fe::RED_BLOCKS, 0, st>>>(pc, pd, s, bc->rtol); fe_count_launch();
-  k_copy<<<gb, 256, 0, st>>>(z, p, n); fe_count_launch();
-  FE_CUDA(cudaGetLastError());
+  double* csum = Ainv ? (double*)(ccnt + nzp) : nullptr;
 
-  // one CG iteration = 9 launches; capture a block of them into a graph
-  auto iteration = [&]() -> fe_status {
-    FE_TRY(fe_poisson_apply_K(m, p, q));
-    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(p, q, n, pa); fe_count_launch();
-    k_fin_alpha<<<1, fe::RED_BLOCKS, 0, st>>>(pa, s); fe_count_launch();
-    k_update_xr<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(phi, r, p, q, mask, s, n, pb); fe_count_launch();
-    if (project) { k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(pb, s, 1.0 / (double)n); fe_count_launch(); }
-    coarse();
-    k_precond<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, z, dinv, mask, s, project, n, pc, pd, cy, plane); fe_count_launch();
-    k_fin_beta<<<1, fe::RED_BLOCKS, 0, st>>>(pc, pd, s); fe_count_launch();
-    k_update_p<<<gb, 256, 0, st>>>(p, z, s, n); fe_count_launch();
+  // double residual r = f - K phi (masked; CEF: minus its mean) and |r|^2 on the host
+  auto residual = [&](double* rr) -> fe_status {
+    FE_TRY(fe_poisson_apply_K(m, phi, q));
+    k_resid0<<<gb, 256, 0, st>>>(f, q, mask, r, n); fe_count_launch();
+    if (project) {
+      k_psum<double><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, nullptr, n, pa); fe_count_launch();
+      k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(pa, sref, 1.0 / (double)n); fe_count_launch();
+      k_sub_mean<<<gb, 256, 0, st>>>(r, sref, n); fe_count_launch();
+    }
+    k_psum<double><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(r, r, n, pb); fe_count_launch();
+    k_fin_rr<<<1, fe::RED_BLOCKS, 0, st>>>(pb, sref); fe_count_launch();
+    CgState h;
+    FE_CUDA(cudaMemcpyAsync(&h, sref, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaStreamSynchronize(st));
+    *rr = h.rr;
     return FE_OK;
   };
-  const int per_graph = 16;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int64_t graph_kernels = 0;
-  if (use_graph) {
-    FE_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    fe_status cst = FE_OK;
-    const int64_t before = fe_kernel_launches();
-    for (int i = 0; i < per_graph && cst == FE_OK; ++i) cst = iteration();
-    // captured launches run only when the graph is replayed
-    graph_kernels = fe_kernel_launches() - before;
-    fe_count_launch(-graph_kernels);
-    cudaError_t e = cudaStreamEndCapture(st, &graph);
-    if (cst != FE_OK) { cudaGetLastError(); if (graph) cudaGraphDestroy(graph); return cst; }
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fe_fail(FE_ECUDA, "CG capture: %s", cudaGetErrorString(e));
-    }
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      cudaGraphDestroy(graph);
-      return fe_fail(FE_ECUDA, "CG graph: %s", cudaGetErrorString(e));
-    }
-  }
+  double rr = 0.0;
+  FE_TRY(residual(&rr));
+  const double bnorm2 = rr;
+  const double tol2 = bc->rtol * bc->rtol * bnorm2;
+  int used = 0;
   CgState hs = {};
-  int launched = 0;
-  fe_status result = FE_OK;
-  while (true) {
-    FE_CUDA(cudaMemcpyAsync(&hs, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
-    FE_CUDA(cudaStreamSynchronize(st));
-    if (hs.done || launched >= bc->max_iter) break;
-    if (use_graph) {
-      cudaError_t e = cudaGraphLaunch(exec, st);
-      if (e != cudaSuccess) { result = fe_fail(FE_ECUDA, "CG graph launch: %s", cudaGetErrorString(e)); break; }
-      fe_count_launch(graph_kernels);
-      launched += per_graph;
-    } else {
-      result = iteration();
-      if (result != FE_OK) break;
-      launched += 1;
+  GraphExec gexec_f, gexec_d;
+  int64_t gk_f = 0, gk_d = 0;
+
+  if (mixed && rr > tol2) {
+    // iterative refinement: float CG on K delta = r to a modest relative accuracy, phi +=
+    // delta, the residual again in double (Section 2.3's K phi = c is solved to rtol in
+    // double; only the corrections are float)
+    float* rf = fl;
+    float* zf = rf + n;
+    float* pf = zf + n;
+    float* qf = pf + n;
+    float* df = qf + n;
+    float* dinvf = df + n;
+    k_to_float<<<gb, 256, 0, st>>>(dinv, dinvf, n); fe_count_launch();
+    CgBuf<float> bf{df, rf, zf, pf, qf, dinvf, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv};
+    constexpr double RTOL_INNER = 1e-4;
+    int stalls = 0, cap = bc->max_iter;
+    for (int outer = 0; outer < 40 && rr > tol2 && used < bc->max_iter; ++outer) {
+      k_to_float<<<gb, 256, 0, st>>>(r, rf, n); fe_count_launch();
+      FE_CUDA(cudaMemsetAsync(df, 0, sizeof(float) * n, st));
+      const int budget = std::min(cap, bc->max_iter - used);
+      FE_TRY(cg_run<float>(m, bf, project, RTOL_INNER, -1.0, budget, use_graph, &gexec_f.e, &gk_f,
+                           &hs));
+      used += hs.iters;
+      if (outer == 0) cap = 2 * hs.iters + 64;   // later corrections need no more than this
+      k_add_delta<<<gb, 256, 0, st>>>(phi, df, mask, n); fe_count_launch();
+      double rr_new = 0.0;
+      FE_TRY(residual(&rr_new));
+      stalls = rr_new > 0.25 * rr ? stalls + 1 : 0;
+      rr = rr_new;
+      if (stalls >= 2) break;   // float corrections no longer help: finish in double
     }
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  if (result != FE_OK) return result;
+  if (rr > tol2 && used < bc->max_iter) {
+    // double CG from the current phi (the whole solve when the mixed mode is off)
+    CgBuf<double> bd{phi, r, z, p, q, dinv, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv};
+    FE_TRY(cg_run<double>(m, bd, project, bc->rtol, tol2, bc->max_iter - used, use_graph,
+                          &gexec_d.e, &gk_d, &hs));
+    used += hs.iters;
+    rr = hs.rr;
+  }
   if (project) {
-    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(m->d_mass, phi, n, pa); fe_count_launch();
-    k_psum<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(m->d_mass, nullptr, n, pb); fe_count_launch();
+    k_psum<double><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(m->d_mass, phi, n, pa); fe_count_launch();
+    k_psum<double><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(m->d_mass, nullptr, n, pb); fe_count_launch();
     k_shift_mean<<<gb, fe::RED_BLOCKS, 0, st>>>(phi, pa, pb, n); fe_count_launch();
   }
   if (vbare) {
@@ -725,14 +864,14 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   }
   FE_CUDA(cudaGetLastError());
   FE_CUDA(cudaStreamSynchronize(st));
-  double rel = hs.bnorm2 > 0 ? std::sqrt(hs.rr / hs.bnorm2) : 0.0;
-  bool conv = hs.bnorm2 == 0.0 || hs.rr <= hs.tol2;
+  double rel = bnorm2 > 0 ? std::sqrt(rr / bnorm2) : 0.0;
+  bool conv = bnorm2 == 0.0 || rr <= tol2;
   if (info) {
-    info->iters = hs.iters;
+    info->iters = used;
     info->rel_residual = rel;
     info->status = conv ? FE_OK : FE_ENOCONV;
   }
   if (!conv)
-    return fe_fail(FE_ENOCONV, "Poisson CG: %d iterations, relative residual %.3e", hs.iters, rel);
+    return fe_fail(FE_ENOCONV, "Poisson CG: %d iterations, relative residual %.3e", used, rel);
   return FE_OK;
 }

@@ -153,3 +153,23 @@ def test_plane_coarse_space_same_solution_fewer_iterations(fe, kind):
         assert np.max(np.abs(phi.cpu().numpy() - ref)) <= 1e-9 * np.max(np.abs(ref))
         iters[planes] = info.iters
     assert iters[True] < 0.7 * iters[False], iters
+
+
+@pytest.mark.parametrize("kind", ["cef", "lcpd"])
+def test_mixed_refinement_matches_double_cg(fe, kind):
+    """Float corrections refined against the double residual reach the double CG's
+    solution: same stopping test, solutions within the residual bound times the
+    conditioning (1e-9 relative)."""
+    base = W.small_slab(ncell=(3, 3, 12), p=4, L=(6.0, 6.0, 24.0), natoms=5, seed=17)
+    bias = {"cef": W.Bias("cef", field=0.01),
+            "lcpd": W.Bias("cpd", dV=0.05, zA=2.0, zB=22.0, patch=((1.0, 1.0), (4.0, 5.0)))}[kind]
+    slab = W.Slab(base.name, base.L, base.ncell, base.p, base.R, base.Z, bias)
+    m = fe.Mesh.from_slab(slab)
+    out = {}
+    for mixed in (False, True):
+        m.set_poisson_mixed(mixed)
+        phi, vb, info = m.poisson_solve(bias, rtol=1e-12)
+        assert info.status == 0 and info.rel_residual <= 1e-12
+        out[mixed] = phi.cpu().numpy()
+    ref = out[False]
+    assert np.max(np.abs(out[True] - ref)) <= 1e-9 * np.max(np.abs(ref))
