@@ -106,12 +106,13 @@ enum { FE_RR_PRODUCTS_F64 = 0, FE_RR_PRODUCTS_TC32 = 1 };
  *     iteration count changes. */
 enum { FE_PRECOND_JACOBI = 0, FE_PRECOND_JACOBI_PLANES = 1 };
 /*   FE_OPT_POISSON_ARITH: arithmetic of the Poisson solve.  FE_POISSON_F64: CG in double.
- *     FE_POISSON_MIXED (default): iterative refinement -- the residual f - K phi and the
- *     update of phi in double, each correction from a float CG (operator, vectors and
- *     preconditioner in float, dot products accumulated in double) run to a relative
- *     residual of 1e-4; when a correction stops reducing the double residual, double CG
- *     finishes from the current phi.  The stopping test (rtol on the double residual) and so
- *     the accuracy of phi are those of FE_POISSON_F64. */
+ *     FE_POISSON_MIXED (default): a float CG (operator, vectors and preconditioner in float,
+ *     dot products accumulated in double) with reliable updates -- whenever its residual has
+ *     dropped by 1e2, phi (double) takes the float iterate and the residual is replaced by
+ *     the double residual f - K phi (the search direction restarts when the two residuals
+ *     have drifted apart); if an update interval stops reducing that residual,
+ *     double CG finishes from the current phi.  The stopping test (rtol on the double
+ *     residual) and so the accuracy of phi are those of FE_POISSON_F64. */
 enum { FE_POISSON_F64 = 0, FE_POISSON_MIXED = 1 };
 fe_status fe_set_option(fe_mesh* mesh, int option, int64_t value);
 
@@ -189,6 +190,18 @@ fe_status fe_batch_apply_H(fe_batch* batch, const void* const* X, void* const* Y
 fe_status fe_batch_cheb_filter(fe_batch* batch, void* const* X, const int64_t* nvec,
                                const int64_t* ld, int degree, const double* a,
                                const double* b, const double* a0, fe_precision prec);
+
+/* Cholesky-QR + Rayleigh-Ritz of every instance (the result of fe_rayleigh_ritz per
+ * instance, Section 2.3's smallest eigenpairs): X host array of n device blocks with the
+ * same nvec, ld host array, eig host array of n device pointers to [nvec] doubles
+ * (ascending Ritz values).  Ht X is one batched launch and the n x n steps are batched
+ * cuBLAS / cuSOLVER calls over all instances.  FE_F64 blocks use double products; FE_F32
+ * blocks need FE_OPT_RR_PRODUCTS = FE_RR_PRODUCTS_TC32 on every mesh (FE_EUNSUPPORTED
+ * otherwise).  An instance whose scaled Gram matrix is not safely positive definite is
+ * redone by fe_rayleigh_ritz.  Uses each mesh's Rayleigh-Ritz workspace and a batch-owned
+ * n x n work array. */
+fe_status fe_batch_rayleigh_ritz(fe_batch* batch, void* const* X, int64_t nvec,
+                                 const int64_t* ld, double* const* eig, fe_precision prec);
 
 typedef enum { FE_BIAS_CEF = 0, FE_BIAS_CPD = 1 } fe_bias_kind;
 

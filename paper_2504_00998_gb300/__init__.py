@@ -254,3 +254,14 @@ class Batch:
         call("fe_batch_cheb_filter", self._h, xp, nvec, ld, int(degree), dd[0], dd[1], dd[2],
              int(prec))
         return Xs
+
+    def rayleigh_ritz(self, Xs, prec=FE_F64):
+        """Cholesky-QR + Rayleigh-Ritz of every block (equal widths); returns the Ritz values
+        per instance."""
+        xp, nvec, ld = self._blocks(Xs, prec)
+        n = Xs[0].shape[1]
+        assert all(X.shape[1] == n for X in Xs)
+        eigs = [torch.empty(n, dtype=torch.float64, device=X.device) for X in Xs]
+        ep = (C.c_void_p * len(eigs))(*[e.data_ptr() for e in eigs])
+        call("fe_batch_rayleigh_ritz", self._h, xp, int(n), ld, ep, int(prec))
+        return eigs

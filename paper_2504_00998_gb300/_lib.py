@@ -32,6 +32,7 @@ EXPORTS = [
     "fe_rayleigh_ritz", "fe_atom_fields", "fe_energy", "fe_atom_fields_vjp",
     "fe_lanczos_bounds", "fe_kernel_launches", "fe_last_error",
     "fe_batch_create", "fe_batch_destroy", "fe_batch_apply_H", "fe_batch_cheb_filter",
+    "fe_batch_rayleigh_ritz",
 ]
 
 
@@ -97,6 +98,7 @@ def load(path=LIB_PATH):
         "fe_batch_destroy": ([P], I),
         "fe_batch_apply_H": ([P, P, P, P, P, I], I),
         "fe_batch_cheb_filter": ([P, P, P, P, I, P, P, P, I], I),
+        "fe_batch_rayleigh_ritz": ([P, P, I64, P, P, I], I),
         "fe_kernel_launches": ([], I64),
         "fe_last_error": ([], C.c_char_p),
     }

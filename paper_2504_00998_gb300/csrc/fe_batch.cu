@@ -20,6 +20,9 @@ struct fe_batch {
   cudaStream_t stream = nullptr;
   void* d_desc = nullptr;   // per-instance descriptors of the pending launches
   size_t desc_bytes = 0;
+  void* d_rr = nullptr;     // n x n work of the batched Rayleigh-Ritz
+  size_t rr_bytes = 0;
+  std::vector<char> h_rr;   // host work of the batched eigensolver
 };
 
 namespace {
@@ -91,12 +94,20 @@ int64_t plan(const fe_batch* b, KronInst<T>* inst) {
 }
 
 template <typename T>
-fe_status launch(const fe_batch* b, const KronInst<T>* d_inst, int64_t total, bool use_z) {
+fe_status launch(const fe_batch* b, const KronInst<T>* d_inst, int64_t total, bool use_z,
+                 bool full) {
   const int n = (int)b->meshes.size();
   if constexpr (sizeof(T) == 8)
-    return fe::kron_batch_f64(b->meshes[0]->coefH, b->p, d_inst, n, total, use_z, b->stream);
+    return fe::kron_batch_f64(b->meshes[0]->coefH, b->p, d_inst, n, total, use_z, full, b->stream);
   else
-    return fe::kron_batch_f32(b->meshes[0]->coefH, b->p, d_inst, n, total, use_z, b->stream);
+    return fe::kron_batch_f32(b->meshes[0]->coefH, b->p, d_inst, n, total, use_z, full, b->stream);
+}
+
+template <typename T>
+bool all_full(const KronInst<T>* inst, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!inst[i].full) return false;
+  return true;
 }
 
 template <typename T>
@@ -111,7 +122,7 @@ fe_status batch_apply(fe_batch* b, const void* const* X, void* const* Y, const i
   FE_TRY(grow_desc(b, n * sizeof(KronInst<T>)));
   FE_CUDA(cudaMemcpyAsync(b->d_desc, inst.data(), n * sizeof(KronInst<T>),
                           cudaMemcpyHostToDevice, b->stream));
-  return launch(b, (const KronInst<T>*)b->d_desc, total, false);
+  return launch(b, (const KronInst<T>*)b->d_desc, total, false, all_full(inst.data(), n));
 }
 
 // The recurrence of fe_cheb_filter, per instance, with every step one batched launch.  All
@@ -160,7 +171,8 @@ fe_status batch_filter(fe_batch* b, void* const* X, const int64_t* nvec, const i
   FE_TRY(grow_desc(b, bytes));
   FE_CUDA(cudaMemcpyAsync(b->d_desc, inst.data(), bytes, cudaMemcpyHostToDevice, b->stream));
   const KronInst<T>* d = (const KronInst<T>*)b->d_desc;
-  for (int s = 0; s < degree; ++s) FE_TRY(launch(b, d + s * n, total, s > 0));
+  const bool full = all_full(inst.data(), n);
+  for (int s = 0; s < degree; ++s) FE_TRY(launch(b, d + s * n, total, s > 0, full));
   for (size_t i = 0; i < n; ++i)
     if (cur[i] != X[i])
       FE_CUDA(cudaMemcpy2DAsync(X[i], ld[i] * eb, cur[i], ld[i] * eb, nvec[i] * eb,
@@ -197,11 +209,12 @@ extern "C" fe_status fe_batch_create(fe_mesh* const* meshes, int n, fe_batch** o
 extern "C" fe_status fe_batch_destroy(fe_batch* b) {
   if (!b) return FE_OK;
   fe_status st = FE_OK;
-  if (b->d_desc) {
+  if (b->d_desc || b->d_rr) {
     if (cudaSetDevice(b->device) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess ||
-        cudaFree(b->d_desc) != cudaSuccess) {
+        (b->d_desc && cudaFree(b->d_desc) != cudaSuccess) ||
+        (b->d_rr && cudaFree(b->d_rr) != cudaSuccess)) {
       cudaGetLastError();
-      st = fe_fail(FE_ECUDA, "fe_batch_destroy: could not release the descriptors");
+      st = fe_fail(FE_ECUDA, "fe_batch_destroy: could not release the batch work arrays");
     }
   }
   delete b;
@@ -245,4 +258,259 @@ extern "C" fe_status fe_batch_cheb_filter(fe_batch* b, void* const* X, const int
   FE_TRY(fe_activate(b->meshes[0]));
   return prec == FE_F64 ? batch_filter<double>(b, X, nvec, ld, degree, a, bnd, a0)
                         : batch_filter<float>(b, X, nvec, ld, degree, a, bnd, a0);
+}
+
+// ---- batched Rayleigh-Ritz ---------------------------------------------------------------------
+// Per instance the same steps as fe_rayleigh_ritz's Gram path: S = X^T X, H = X^T (Ht X), the
+// scaled Gram matrix D S D = R^T R (Cholesky), G = R^-T (D H D) R^-1 = Q diag(eig) Q^T, and
+// X <- X D R^-1 Q.  Ht X is one batched operator launch; the n x n steps are batched cuBLAS /
+// cuSOLVER calls over all instances; only the block products run per instance.
+namespace {
+
+__global__ void k_b_f2d(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+__global__ void k_b_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+// d = 1/sqrt(diag S) per matrix
+__global__ void k_b_invsqrt_diag(const double* __restrict__ S, int n, int nb, double* __restrict__ d) {
+  const int64_t tot = (int64_t)n * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / n, j = t % n;
+    const double v = S[b * n * n + j * n + j];
+    d[t] = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+  }
+}
+// S <- D S D and H <- D sym(H) D (column-major n x n, both triangles)
+__global__ void k_b_scale(double* __restrict__ S, double* __restrict__ H, const double* __restrict__ d,
+                          int n, int nb) {
+  const int64_t tot = (int64_t)n * n * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / ((int64_t)n * n), r = t % ((int64_t)n * n);
+    const int i = (int)(r % n), j = (int)(r / n);
+    if (i > j) continue;   // one thread per unordered pair
+    const double di = d[b * n + i], dj = d[b * n + j];
+    double* Sb = S + b * n * n;
+    double* Hb = H + b * n * n;
+    const double s = 0.5 * (Sb[i + (int64_t)j * n] + Sb[j + (int64_t)i * n]) * di * dj;
+    const double h = 0.5 * (Hb[i + (int64_t)j * n] + Hb[j + (int64_t)i * n]) * di * dj;
+    Sb[i + (int64_t)j * n] = s;
+    Sb[j + (int64_t)i * n] = s;
+    Hb[i + (int64_t)j * n] = h;
+    Hb[j + (int64_t)i * n] = h;
+  }
+}
+__global__ void k_b_symm(double* __restrict__ G, int n, int nb) {
+  const int64_t tot = (int64_t)n * n * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / ((int64_t)n * n), r = t % ((int64_t)n * n);
+    const int i = (int)(r % n), j = (int)(r / n);
+    if (i >= j) continue;
+    double* Gb = G + b * n * n;
+    const double v = 0.5 * (Gb[i + (int64_t)j * n] + Gb[j + (int64_t)i * n]);
+    Gb[i + (int64_t)j * n] = v;
+    Gb[j + (int64_t)i * n] = v;
+  }
+}
+// row i of every C scaled by d_i; the diagonal of every R into rd
+__global__ void k_b_rowscale(double* __restrict__ C, const double* __restrict__ d, int n, int nb) {
+  const int64_t tot = (int64_t)n * n * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / ((int64_t)n * n), r = t % ((int64_t)n * n);
+    C[t] *= d[b * n + (r % n)];
+  }
+}
+__global__ void k_b_diag(const double* __restrict__ R, int n, int nb, double* __restrict__ rd) {
+  const int64_t tot = (int64_t)n * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / n, j = t % n;
+    rd[t] = R[b * n * n + j * n + j];
+  }
+}
+
+int grid_of(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
+}
+
+}  // namespace
+
+extern "C" fe_status fe_batch_rayleigh_ritz(fe_batch* b, void* const* X, int64_t nvec,
+                                            const int64_t* ld, double* const* eig,
+                                            fe_precision prec) {
+  if (!b || !eig) return fe_fail(FE_EINVAL, "fe_batch_rayleigh_ritz: null argument");
+  if (prec != FE_F64 && prec != FE_F32)
+    return fe_fail(FE_EUNSUPPORTED, "fe_batch_rayleigh_ritz: FE_F64 and FE_F32 only");
+  const int nb = (int)b->meshes.size();
+  if (prec == FE_F32)
+    for (int i = 0; i < nb; ++i)
+      if (b->meshes[i]->rr_products != FE_RR_PRODUCTS_TC32)
+        return fe_fail(FE_EUNSUPPORTED, "fe_batch_rayleigh_ritz: float blocks need the tensor-core "
+                       "block products (FE_OPT_RR_PRODUCTS = FE_RR_PRODUCTS_TC32) on every mesh");
+  if (nvec < 1 || nvec > 4096) return fe_fail(FE_EINVAL, "fe_batch_rayleigh_ritz: need 1 <= nvec <= 4096");
+  std::vector<int64_t> nv(nb, nvec);
+  FE_TRY(check_blocks(b, (const void* const*)X, nv.data(), ld, prec, "fe_batch_rayleigh_ritz"));
+  for (int i = 0; i < nb; ++i) {
+    if (!eig[i]) return fe_fail(FE_EINVAL, "fe_batch_rayleigh_ritz: instance %d: null eig", i);
+    if (nvec > b->meshes[i]->n_psi)
+      return fe_fail(FE_EINVAL, "fe_batch_rayleigh_ritz: instance %d: nvec exceeds the node count", i);
+  }
+  FE_TRY(fe_activate(b->meshes[0]));
+  fe_mesh* m0 = b->meshes[0];
+  cudaStream_t st = b->stream;
+  const int n = (int)nvec;
+  const int64_t nn = (int64_t)n * n;
+  const int eb = prec == FE_F64 ? 8 : 4;
+
+  // Ht X of every instance (one launch), into each mesh's workspace: [HX | rotation tmp]
+  std::vector<void*> hx(nb), tmp(nb);
+  for (int i = 0; i < nb; ++i) {
+    void* w;
+    const size_t blk = (size_t)b->meshes[i]->n_psi * ld[i] * eb;
+    FE_TRY(fe_ws(b->meshes[i], WS_RR_HX, 2 * blk, &w));
+    hx[i] = w;
+    tmp[i] = (char*)w + blk;
+  }
+  if (prec == FE_F64) FE_TRY(batch_apply<double>(b, X, hx.data(), nv.data(), ld));
+  else FE_TRY(batch_apply<float>(b, X, hx.data(), nv.data(), ld));
+
+  // batch work: S, H (double), Sf, Hf (float), d, W, R diagonals, pointer arrays, infos
+  size_t bytes = sizeof(double) * (2 * nn * nb + 3 * (size_t)n * nb) + sizeof(float) * 2 * nn * nb +
+                 sizeof(double*) * 2 * nb + sizeof(int) * 2 * nb + 1024;
+  size_t dev_syev = 0, host_syev = 0;
+  cusolverDnParams_t params = nullptr;
+  FE_CUSOLVER(cusolverDnCreateParams(&params));
+  struct ParamsGuard { cusolverDnParams_t p; ~ParamsGuard() { if (p) cusolverDnDestroyParams(p); } } pg{params};
+  FE_CUSOLVER(cusolverDnXsyevBatched_bufferSize(m0->cusolver, params, CUSOLVER_EIG_MODE_VECTOR,
+                                                CUBLAS_FILL_MODE_UPPER, n, CUDA_R_64F, nullptr, n,
+                                                CUDA_R_64F, nullptr, CUDA_R_64F, &dev_syev,
+                                                &host_syev, nb));
+  bytes += dev_syev + 256;
+  if (b->rr_bytes < bytes) {
+    if (b->d_rr) {
+      FE_CUDA(cudaStreamSynchronize(st));
+      FE_CUDA(cudaFree(b->d_rr));
+      b->d_rr = nullptr;
+      b->rr_bytes = 0;
+    }
+    if (cudaMalloc(&b->d_rr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fe_fail(FE_ENOMEM, "batched Rayleigh-Ritz work of %zu bytes could not be allocated", bytes);
+    }
+    b->rr_bytes = bytes;
+  }
+  if (b->h_rr.size() < host_syev + 1) b->h_rr.resize(host_syev + 1);
+  double* S = (double*)b->d_rr;
+  double* H = S + nn * nb;
+  double* d = H + nn * nb;
+  double* W = d + (size_t)n * nb;
+  double* rd = W + (size_t)n * nb;
+  float* Sf = (float*)(rd + (size_t)n * nb);
+  float* Hf = Sf + nn * nb;
+  double** pS = (double**)(((uintptr_t)(Hf + nn * nb) + 15) & ~(uintptr_t)15);
+  double** pH = pS + nb;
+  int* info = (int*)(pH + nb);
+  void* syev_ws = (void*)(((uintptr_t)(info + 2 * nb) + 255) & ~(uintptr_t)255);
+  std::vector<double*> hS(nb), hH(nb);
+  for (int i = 0; i < nb; ++i) { hS[i] = S + nn * i; hH[i] = H + nn * i; }
+  FE_CUDA(cudaMemcpyAsync(pS, hS.data(), sizeof(double*) * nb, cudaMemcpyHostToDevice, st));
+  FE_CUDA(cudaMemcpyAsync(pH, hH.data(), sizeof(double*) * nb, cudaMemcpyHostToDevice, st));
+
+  // block products
+  for (int i = 0; i < nb; ++i) {
+    const int N = (int)b->meshes[i]->n_psi;
+    if (prec == FE_F64) {
+      const double one = 1.0, zero = 0.0;
+      FE_CUBLAS(cublasDgemm(m0->cublas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, N, &one, (const double*)X[i],
+                            (int)ld[i], (const double*)X[i], (int)ld[i], &zero, hS[i], n));
+      FE_CUBLAS(cublasDgemm(m0->cublas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, N, &one, (const double*)X[i],
+                            (int)ld[i], (const double*)hx[i], (int)ld[i], &zero, hH[i], n));
+    } else {
+      const float one = 1.0f, zero = 0.0f;
+      const cublasComputeType_t ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+      FE_CUBLAS(cublasGemmEx(m0->cublas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, N, &one, X[i], CUDA_R_32F,
+                             (int)ld[i], X[i], CUDA_R_32F, (int)ld[i], &zero, Sf + nn * i, CUDA_R_32F,
+                             n, ct, CUBLAS_GEMM_DEFAULT));
+      FE_CUBLAS(cublasGemmEx(m0->cublas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, N, &one, X[i], CUDA_R_32F,
+                             (int)ld[i], hx[i], CUDA_R_32F, (int)ld[i], &zero, Hf + nn * i, CUDA_R_32F,
+                             n, ct, CUBLAS_GEMM_DEFAULT));
+    }
+  }
+  const int64_t tot = nn * nb;
+  if (prec == FE_F32) {
+    k_b_f2d<<<grid_of(tot), 256, 0, st>>>(Sf, S, tot); fe_count_launch();
+    k_b_f2d<<<grid_of(tot), 256, 0, st>>>(Hf, H, tot); fe_count_launch();
+  }
+  k_b_invsqrt_diag<<<grid_of((int64_t)n * nb), 256, 0, st>>>(S, n, nb, d); fe_count_launch();
+  k_b_scale<<<grid_of(tot), 256, 0, st>>>(S, H, d, n, nb); fe_count_launch();
+  FE_CUSOLVER(cusolverDnDpotrfBatched(m0->cusolver, CUBLAS_FILL_MODE_UPPER, n, pS, n, info, nb));
+  k_b_diag<<<grid_of((int64_t)n * nb), 256, 0, st>>>(S, n, nb, rd); fe_count_launch();
+  std::vector<int> hinfo(nb);
+  std::vector<double> hrd((size_t)n * nb);
+  FE_CUDA(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+  FE_CUDA(cudaMemcpyAsync(hrd.data(), rd, sizeof(double) * n * nb, cudaMemcpyDeviceToHost, st));
+  FE_CUDA(cudaStreamSynchronize(st));
+  // an instance whose scaled Gram matrix is not safely positive definite is redone alone
+  std::vector<char> ill(nb, 0);
+  for (int i = 0; i < nb; ++i) {
+    double rmax = 0.0, rmin = 1e300;
+    for (int j = 0; j < n; ++j) {
+      rmax = std::fmax(rmax, std::fabs(hrd[(size_t)i * n + j]));
+      rmin = std::fmin(rmin, std::fabs(hrd[(size_t)i * n + j]));
+    }
+    ill[i] = hinfo[i] != 0 || !(rmin > 0.0) || (rmax / rmin) * (rmax / rmin) > 1e8;
+  }
+  const double one = 1.0;
+  // G = R^-T H R^-1
+  FE_CUBLAS(cublasDtrsmBatched(m0->cublas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T,
+                               CUBLAS_DIAG_NON_UNIT, n, n, &one, pS, n, pH, n, nb));
+  FE_CUBLAS(cublasDtrsmBatched(m0->cublas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                               CUBLAS_DIAG_NON_UNIT, n, n, &one, pS, n, pH, n, nb));
+  k_b_symm<<<grid_of(tot), 256, 0, st>>>(H, n, nb); fe_count_launch();
+  FE_CUSOLVER(cusolverDnXsyevBatched(m0->cusolver, params, CUSOLVER_EIG_MODE_VECTOR,
+                                     CUBLAS_FILL_MODE_UPPER, n, CUDA_R_64F, H, n, CUDA_R_64F, W,
+                                     CUDA_R_64F, syev_ws, dev_syev, b->h_rr.data(), host_syev,
+                                     info + nb, nb));
+  // C = D R^-1 Q
+  FE_CUBLAS(cublasDtrsmBatched(m0->cublas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                               CUBLAS_DIAG_NON_UNIT, n, n, &one, pS, n, pH, n, nb));
+  k_b_rowscale<<<grid_of(tot), 256, 0, st>>>(H, d, n, nb); fe_count_launch();
+  if (prec == FE_F32) { k_b_d2f<<<grid_of(tot), 256, 0, st>>>(H, Hf, tot); fe_count_launch(); }
+  FE_CUDA(cudaGetLastError());
+  // X <- X C and the Ritz values, for the well-conditioned instances
+  for (int i = 0; i < nb; ++i) {
+    if (ill[i]) continue;
+    const int N = (int)b->meshes[i]->n_psi;
+    if (prec == FE_F64) {
+      const double zero = 0.0;
+      FE_CUBLAS(cublasDgemm(m0->cublas, CUBLAS_OP_T, CUBLAS_OP_N, n, N, n, &one, hH[i], n,
+                            (const double*)X[i], (int)ld[i], &zero, (double*)tmp[i], (int)ld[i]));
+    } else {
+      const float onef = 1.0f, zerof = 0.0f;
+      FE_CUBLAS(cublasGemmEx(m0->cublas, CUBLAS_OP_T, CUBLAS_OP_N, n, N, n, &onef, Hf + nn * i,
+                             CUDA_R_32F, n, X[i], CUDA_R_32F, (int)ld[i], &zerof, tmp[i], CUDA_R_32F,
+                             (int)ld[i], CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT));
+    }
+    FE_CUDA(cudaMemcpy2DAsync(X[i], ld[i] * eb, tmp[i], ld[i] * eb, (size_t)n * eb, N,
+                              cudaMemcpyDeviceToDevice, st));
+    FE_CUDA(cudaMemcpyAsync(eig[i], W + (size_t)i * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  }
+  FE_CUDA(cudaMemcpyAsync(hinfo.data(), info + nb, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+  FE_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < nb; ++i)
+    if (!ill[i] && hinfo[i] != 0)
+      return fe_fail(FE_ECUDA, "fe_batch_rayleigh_ritz: instance %d: eigensolver info %d", i, hinfo[i]);
+  for (int i = 0; i < nb; ++i)
+    if (ill[i]) FE_TRY(fe_rayleigh_ritz(b->meshes[i], X[i], nvec, ld[i], eig[i], prec));
+  return FE_OK;
 }

@@ -97,6 +97,7 @@ struct KronInst {
   KronIO<T> io;
   int64_t cta0;              // first CTA of this instance in the batched 1D grid
   int64_t nvt;               // vector tiles of this instance
+  int full;                  // complete xy blocks and vector tiles (set by the plan)
 };
 
 
@@ -119,9 +120,9 @@ fe_status kron_k1f(const KronCoef& cf, const KronGeom& g, const KronIO<float>& i
 int64_t kron_batch_plan_f64(int p, KronInst<double>* inst, int n);
 int64_t kron_batch_plan_f32(int p, KronInst<float>* inst, int n);
 fe_status kron_batch_f64(const KronCoef& cf, int p, const KronInst<double>* d_inst, int n,
-                         int64_t total_ctas, bool use_z, cudaStream_t st);
+                         int64_t total_ctas, bool use_z, bool full, cudaStream_t st);
 fe_status kron_batch_f32(const KronCoef& cf, int p, const KronInst<float>* d_inst, int n,
-                         int64_t total_ctas, bool use_z, cudaStream_t st);
+                         int64_t total_ctas, bool use_z, bool full, cudaStream_t st);
 }  // namespace fe
 
 // ---- the mesh ---------------------------------------------------------------------------

@@ -174,7 +174,9 @@ struct KronTileT {
 };
 
 // One CTA's work: xy block bxy (x fastest), vector tile vti, z segment zsi.
-template <typename T, int CH, class TL>
+// FULL: every xy block is complete and every vector tile full, so no ownership, edge or
+// ragged-vector test is needed anywhere in the sweep
+template <typename T, int CH, class TL, bool FULL>
 __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom& g,
                                           const KronIO<T>& io, int bxy, int vti, int zsi) {
   using C = Chunk<T, CH>;
@@ -216,7 +218,8 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
     const int gx = pmod(x0 - P + xh, g.NX), gy = pmod(y0 - P + yh, g.NY);
     const int64_t v0 = vt0 + (int64_t)ch * CH;
     const int64_t rem = io.nvec - v0;
-    s_bytes[i] = e >= NST ? -1 : (rem <= 0 ? 0 : (rem >= CH ? CHB : (int)(rem * sizeof(T))));
+    s_bytes[i] = e >= NST ? -1
+                          : (FULL ? CHB : (rem <= 0 ? 0 : (rem >= CH ? CHB : (int)(rem * sizeof(T)))));
     s_goff[i] = (gx + (int64_t)g.NX * gy) * io.ldx + v0;
   }
 
@@ -237,7 +240,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
     it_x[i] = node % BXn;
     it_y[i] = node / BXn;
     const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
-    it_own[i] = valid && (x0 + it_x[i] < g.NX) && (y0 + it_y[i] < g.NY) && (v0 < io.nvec);
+    it_own[i] = valid && (FULL || ((x0 + it_x[i] < g.NX) && (y0 + it_y[i] < g.NY) && (v0 < io.nvec)));
     it_node[i] = (x0 + it_x[i]) + (int64_t)g.NX * (y0 + it_y[i]);
     it_yo[i] = it_node[i] * io.ldy + v0;
     it_sxy[i] = cf.mass_scale ? cf.sig[it_x[i] % P] * cf.sig[it_y[i] % P] : T(1);
@@ -280,7 +283,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
     if (use_v && tid < BXn * BYn) {
       const int x = tid % BXn, y = tid / BXn;
       T* vd = Vs + ((gz - gbeg) % TL::NSB) * (BXn * BYn) + tid;
-      const bool ok = x0 + x < g.NX && y0 + y < g.NY;
+      const bool ok = FULL || (x0 + x < g.NX && y0 + y < g.NY);
       const int64_t nid = (int64_t)zs * plane_nodes + (x0 + x) + (int64_t)g.NX * (y0 + y);
       cp_async<(int)sizeof(T)>(vd, ok ? io.V + nid : io.V, ok ? (int)sizeof(T) : 0);
     }
@@ -292,7 +295,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
         if (item >= NZI) continue;
         const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
         const int64_t rem = io.nvec - v0;
-        const int nb = (!it_own[i] || rem <= 0) ? 0 : (rem >= CH ? CHB : (int)(rem * sizeof(T)));
+        const int nb = !it_own[i] ? 0 : (FULL ? CHB : (rem <= 0 ? 0 : (rem >= CH ? CHB : (int)(rem * sizeof(T)))));
         const T* src = nb ? io.Z + ((int64_t)zs * plane_nodes + it_node[i]) * io.ldz + v0 : io.Z;
         cp_async<CHB>(zd + item, src, nb);
       }
@@ -320,7 +323,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
         for (int e = 0; e < CH; ++e) out.v[e] = C::fma_t(io.beta, zc.v[e], out.v[e]);
       }
       T* yp = yplane + it_yo[i];
-      if (v0 + CH <= io.nvec) {
+      if (FULL || v0 + CH <= io.nvec) {
         *reinterpret_cast<C*>(yp) = out;
       } else {
         for (int e = 0; e < CH; ++e)
@@ -545,19 +548,19 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
 // 1D grid, vector tile fastest: the CTAs that read the other halves of a node's DRAM
 // bursts (neighbouring vector tiles of the same xy block) run side by side, so a burst is
 // fetched once; neighbouring xy blocks (halo sharing) follow within the resident window.
-template <typename T, int CH, class TL>
+template <typename T, int CH, class TL, bool FULL>
 __global__ void __launch_bounds__(TL::NTHR)
 kron_kernel(const KronCoefT<T> cf, const KronGeom g, const KronIO<T> io, int nvt) {
   const int b = blockIdx.x;
   const int nxy = g.nbx * g.nby;
   const int r = b / nvt;
-  kron_body<T, CH, TL>(cf, g, io, r % nxy, b % nvt, r / nxy);
+  kron_body<T, CH, TL, FULL>(cf, g, io, r % nxy, b % nvt, r / nxy);
 }
 
 // Batched form: many independent meshes that share p and the cell size (so one coefficient
 // table) in one launch.  The 1D grid concatenates the instances' CTA grids; a CTA finds its
 // instance by binary search over the ascending first-CTA offsets.
-template <typename T, int CH, class TL>
+template <typename T, int CH, class TL, bool FULL>
 __global__ void __launch_bounds__(TL::NTHR)
 kron_batch_kernel(const KronCoefT<T> cf, const KronInst<T>* __restrict__ inst, int ninst) {
   const int64_t b = blockIdx.x;
@@ -572,7 +575,7 @@ kron_batch_kernel(const KronCoefT<T> cf, const KronInst<T>* __restrict__ inst, i
   const int nxy = g.nbx * g.nby;
   const int64_t nvt = inst[lo].nvt;
   const int64_t r = local / nvt;
-  kron_body<T, CH, TL>(cf, g, io, (int)(r % nxy), (int)(local % nvt), (int)(r / nxy));
+  kron_body<T, CH, TL, FULL>(cf, g, io, (int)(r % nxy), (int)(local % nvt), (int)(r / nxy));
 }
 
 // Dynamic shared memory limit, and the largest shared-memory carveout so that the residency
@@ -610,9 +613,10 @@ fe_status kron_launch_t(const KronCoef& cf, const KronGeom& g, const KronIO<T>& 
   if (io2.Z != nullptr && io2.beta == T(0)) io2.Z = nullptr;
   const size_t smem = kron_smem<T, CH, TL>(io2.Z != nullptr, io2.V != nullptr);
   if (smem > 227 * 1024) return fe_fail(FE_EINVAL, "tile needs %zu bytes of shared memory", smem);
-  auto kern = kron_kernel<T, CH, TL>;
-  FE_TRY(kron_func_setup(kern, smem));
   const int64_t vtile = (int64_t)TL::NCH * CH;
+  const bool full = g.NX % TL::BXn == 0 && g.NY % TL::BYn == 0 && io.nvec % vtile == 0;
+  auto kern = full ? kron_kernel<T, CH, TL, true> : kron_kernel<T, CH, TL, false>;
+  FE_TRY(kron_func_setup(kern, smem));
   const int64_t nvt = (io.nvec + vtile - 1) / vtile;
   const int64_t total = (int64_t)g.nbx * g.nby * nvt * ((g.nz + g.zseg - 1) / g.zseg);
   if (total > 0x7fffffffLL || nvt > 0x7fffffffLL) return fe_fail(FE_EINVAL, "grid too large");
@@ -684,6 +688,8 @@ int64_t kron_batch_plan_t(KronInst<T>* inst, int n) {
     g.nbx = (g.NX / g.p + TL::BX - 1) / TL::BX;
     g.nby = (g.NY / g.p + TL::BY - 1) / TL::BY;
     inst[i].nvt = (inst[i].io.nvec + (int64_t)TL::NCH * CH - 1) / ((int64_t)TL::NCH * CH);
+    inst[i].full = g.NX % TL::BXn == 0 && g.NY % TL::BYn == 0 &&
+                   inst[i].io.nvec % ((int64_t)TL::NCH * CH) == 0;
     nzmax = g.nz > nzmax ? g.nz : nzmax;
   }
   const int64_t want = 4 * (int64_t)device_sms();
@@ -709,11 +715,11 @@ int64_t kron_batch_plan_t(KronInst<T>* inst, int n) {
 
 template <typename T, int CH, class TL>
 fe_status kron_batch_launch_t(const KronCoef& cf, const KronInst<T>* d_inst, int n,
-                              int64_t total, bool use_z, cudaStream_t st) {
+                              int64_t total, bool use_z, bool full, cudaStream_t st) {
   const size_t smem = kron_smem<T, CH, TL>(use_z, true);
   if (smem > 227 * 1024) return fe_fail(FE_EINVAL, "tile needs %zu bytes of shared memory", smem);
   if (total < 1 || total > 0x7fffffffLL) return fe_fail(FE_EINVAL, "batched grid of %lld CTAs", (long long)total);
-  auto kern = kron_batch_kernel<T, CH, TL>;
+  auto kern = full ? kron_batch_kernel<T, CH, TL, true> : kron_batch_kernel<T, CH, TL, false>;
   FE_TRY(kron_func_setup(kern, smem));
   KronCoefT<T> cft = convert_coef<T>(cf);
   kern<<<(unsigned)total, TL::NTHR, smem, st>>>(cft, d_inst, n); fe_count_launch();
@@ -737,12 +743,12 @@ int64_t kron_batch_plan_dispatch(int p, KronInst<T>* inst, int n) {
 
 template <typename T, int CH, int NCH>
 fe_status kron_batch_dispatch(const KronCoef& cf, int p, const KronInst<T>* d_inst, int n,
-                              int64_t total, bool use_z, cudaStream_t st) {
+                              int64_t total, bool use_z, bool full, cudaStream_t st) {
   switch (p) {
 #define FE_BCASE(pp)                                                                      \
   case pp:                                                                                \
     return kron_batch_launch_t<T, CH, typename KronTileFor<pp, NCH, CH>::type>(cf, d_inst, n, \
-                                                                          total, use_z, st);
+                                                                          total, use_z, full, st);
     FE_BCASE(1) FE_BCASE(2) FE_BCASE(3) FE_BCASE(4) FE_BCASE(5) FE_BCASE(6)
 #undef FE_BCASE
     default: return fe_fail(FE_EUNSUPPORTED, "p = %d", p);

@@ -13,8 +13,8 @@ int64_t kron_batch_plan_f32(int p, KronInst<float>* inst, int n) {
 }
 
 fe_status kron_batch_f32(const KronCoef& cf, int p, const KronInst<float>* d_inst, int n,
-                         int64_t total_ctas, bool use_z, cudaStream_t st) {
-  return kron_batch_dispatch<float, 4, 2>(cf, p, d_inst, n, total_ctas, use_z, st);
+                         int64_t total_ctas, bool use_z, bool full, cudaStream_t st) {
+  return kron_batch_dispatch<float, 4, 2>(cf, p, d_inst, n, total_ctas, use_z, full, st);
 }
 
 }  // namespace fe

@@ -307,6 +307,16 @@ __global__ void k_fin_rr(const double* part, CgState* s) {
   double v = block_sum_partials(part);
   if (threadIdx.x == 0) s->rr = v;
 }
+// residual replacement in a running CG: new r.z and |r|^2, the search direction is kept
+__global__ void k_fin_replace(const double* part_rz, const double* part_rr, CgState* s) {
+  double rz = block_sum_partials(part_rz);
+  double rr = block_sum_partials(part_rr);
+  if (threadIdx.x == 0) {
+    s->rz = rz;
+    s->rr = rr;
+    s->done = (rr == 0.0 || s->iters >= s->maxit) ? 1 : 0;
+  }
+}
 
 // CEF: phi -= (M . phi) / sum M
 __global__ void k_shift_mean(double* __restrict__ phi, const double* part_mphi,
@@ -637,10 +647,17 @@ fe_status apply_K_v(fe_mesh* m, const float* x, float* y) {
 // the first preconditioner call for CEF).  Stops at |r|^2 <= tol2_abs, or (tol2_abs <= 0)
 // |r|^2 <= rtol^2 |r0|^2, or after maxit iterations.  Blocks of iterations replay a CUDA graph
 // captured on first use (*exec, kept by the caller for the rest of the solve).
-template <typename V>
+// Between blocks of iterations the optional hook sees the state and chooses: CG_CONTINUE,
+// CG_STOP, CG_REPLACED (it has written a new residual into b.r: the run recomputes its
+// preconditioned form and r.z and continues with the same search direction) or
+// CG_RESTARTED (the same, and the search direction restarts from the new preconditioned
+// residual).
+enum { CG_CONTINUE = 0, CG_STOP = 1, CG_REPLACED = 2, CG_RESTARTED = 3 };
+
+template <typename V, typename Hook>
 fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double tol2_abs,
                  int maxit, bool use_graph, cudaGraphExec_t* exec, int64_t* graph_kernels,
-                 CgState* out) {
+                 CgState* out, Hook&& hook) {
   const int64_t n = m->n_phi;
   const int64_t plane = (int64_t)m->NX * m->NY;
   const int nzp = m->NZ;
@@ -707,11 +724,28 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
       return fe_fail(FE_ECUDA, "CG graph: %s", cudaGetErrorString(e));
     }
   }
+  auto replaced = [&](bool restart) {
+    if (project) {
+      k_psum<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, nullptr, n, b.pa); fe_count_launch();
+      k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(b.pa, b.s, 1.0 / (double)n); fe_count_launch();
+    }
+    coarse();
+    k_precond<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project,
+                                                             n, b.pc, b.pd, cy, plane); fe_count_launch();
+    k_fin_replace<<<1, fe::RED_BLOCKS, 0, st>>>(b.pc, b.pd, b.s); fe_count_launch();
+    if (restart) { k_copy<V><<<gb, 256, 0, st>>>(b.z, b.p, n); fe_count_launch(); }
+  };
   int launched = 0;
   while (true) {
     FE_CUDA(cudaMemcpyAsync(out, b.s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     FE_CUDA(cudaStreamSynchronize(st));
-    if (out->done || launched >= maxit) break;
+    int action = out->done ? CG_STOP : CG_CONTINUE;
+    FE_TRY(hook(*out, &action));
+    if (action == CG_STOP || launched >= maxit) break;
+    if (action == CG_REPLACED || action == CG_RESTARTED) {
+      replaced(action == CG_RESTARTED);
+      FE_CUDA(cudaGetLastError());
+    }
     if (use_graph) {
       cudaError_t e = cudaGraphLaunch(*exec, st);
       if (e != cudaSuccess) return fe_fail(FE_ECUDA, "CG graph launch: %s", cudaGetErrorString(e));
@@ -815,10 +849,16 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   GraphExec gexec_f, gexec_d;
   int64_t gk_f = 0, gk_d = 0;
 
+  auto no_hook = [](const CgState&, int*) { return FE_OK; };
   if (mixed && rr > tol2) {
-    // iterative refinement: float CG on K delta = r to a modest relative accuracy, phi +=
-    // delta, the residual again in double (Section 2.3's K phi = c is solved to rtol in
-    // double; only the corrections are float)
+    // One float CG (operator, vectors and preconditioner in float; dot products in double)
+    // whose residual is replaced by the double residual f - K phi whenever the float
+    // residual has dropped by 1e2 since the last replacement (reliable updates, Sleijpen
+    // and van der Vorst 1996): phi accumulates the float iterate in double and the stopping
+    // test is on the double residual.  The Krylov direction is kept across a replacement
+    // while the float recurrence still tracks the true residual (within 2x in norm) and
+    // restarted otherwise.  When a replacement interval stops reducing the double
+    // residual, the double CG finishes from the current phi.
     float* rf = fl;
     float* zf = rf + n;
     float* pf = zf + n;
@@ -826,30 +866,38 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
     float* df = qf + n;
     float* dinvf = df + n;
     k_to_float<<<gb, 256, 0, st>>>(dinv, dinvf, n); fe_count_launch();
+    k_to_float<<<gb, 256, 0, st>>>(r, rf, n); fe_count_launch();
+    FE_CUDA(cudaMemsetAsync(df, 0, sizeof(float) * n, st));
     CgBuf<float> bf{df, rf, zf, pf, qf, dinvf, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv};
-    constexpr double RTOL_INNER = 1e-4;
-    int stalls = 0, cap = bc->max_iter;
-    for (int outer = 0; outer < 40 && rr > tol2 && used < bc->max_iter; ++outer) {
-      k_to_float<<<gb, 256, 0, st>>>(r, rf, n); fe_count_launch();
-      FE_CUDA(cudaMemsetAsync(df, 0, sizeof(float) * n, st));
-      const int budget = std::min(cap, bc->max_iter - used);
-      FE_TRY(cg_run<float>(m, bf, project, RTOL_INNER, -1.0, budget, use_graph, &gexec_f.e, &gk_f,
-                           &hs));
-      used += hs.iters;
-      if (outer == 0) cap = 2 * hs.iters + 64;   // later corrections need no more than this
+    double rr_last = rr;
+    int it_last = 0, stalls = 0;
+    auto reliable = [&](const CgState& cs, int* action) -> fe_status {
+      used = cs.iters;
+      const bool trigger = cs.done || cs.rr <= 1e-4 * rr_last || cs.iters - it_last >= 512;
+      if (!trigger) { *action = CG_CONTINUE; return FE_OK; }
       k_add_delta<<<gb, 256, 0, st>>>(phi, df, mask, n); fe_count_launch();
-      double rr_new = 0.0;
-      FE_TRY(residual(&rr_new));
-      stalls = rr_new > 0.25 * rr ? stalls + 1 : 0;
-      rr = rr_new;
-      if (stalls >= 2) break;   // float corrections no longer help: finish in double
-    }
+      FE_CUDA(cudaMemsetAsync(df, 0, sizeof(float) * n, st));
+      FE_TRY(residual(&rr));
+      if (rr <= tol2 || cs.iters >= bc->max_iter) { *action = CG_STOP; return FE_OK; }
+      stalls = rr > 0.25 * rr_last ? stalls + 1 : 0;
+      if (stalls >= 2) { *action = CG_STOP; return FE_OK; }
+      // keep the search direction only while the float recurrence still tracks the true
+      // residual; a larger gap would scale the next step by their ratio, so restart
+      const bool tracks = rr <= 4.0 * cs.rr;
+      rr_last = rr;
+      it_last = cs.iters;
+      k_to_float<<<gb, 256, 0, st>>>(r, rf, n); fe_count_launch();
+      *action = tracks ? CG_REPLACED : CG_RESTARTED;
+      return FE_OK;
+    };
+    FE_TRY(cg_run<float>(m, bf, project, 0.0, tol2, bc->max_iter, use_graph, &gexec_f.e, &gk_f,
+                         &hs, reliable));
   }
   if (rr > tol2 && used < bc->max_iter) {
     // double CG from the current phi (the whole solve when the mixed mode is off)
     CgBuf<double> bd{phi, r, z, p, q, dinv, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv};
     FE_TRY(cg_run<double>(m, bd, project, bc->rtol, tol2, bc->max_iter - used, use_graph,
-                          &gexec_d.e, &gk_d, &hs));
+                          &gexec_d.e, &gk_d, &hs, no_hook));
     used += hs.iters;
     rr = hs.rr;
   }

@@ -173,3 +173,43 @@ def test_bias_sweep_full_size_sampled_rows(fe):
         meshes[k].cheb_filter(singles[k], 20, a[k], bb[k], a0[k], prec=fe.FE_F32)
         d = torch.linalg.norm((Xs[k] - singles[k]).double()) / torch.linalg.norm(singles[k].double())
         assert d <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batch_rayleigh_ritz_matches_per_instance(fe, prec):
+    """Batched Cholesky-QR + Rayleigh-Ritz (batched n x n steps) against fe_rayleigh_ritz per
+    instance: same Ritz values (1e-10 in FP64; 1e-6 relative with float blocks, both through
+    the FP32-accurate tensor-core products), orthonormal rotated blocks whose Rayleigh
+    quotients are the Ritz values."""
+    P = fe.FE_F64 if prec == "f64" else fe.FE_F32
+    dt = fe.storage_dtype(P)
+    inst = _instances(fe, [5, 7, 4], p=3, seed=21)
+    rng = np.random.default_rng(6)
+    nvec = 8
+    Xs = []
+    for om, V, m in inst:
+        m.set_rr_products(True)
+        Xs.append(torch.tensor(rng.standard_normal((om.n_psi, nvec)), dtype=dt, device="cuda"))
+    singles = [X.clone() for X in Xs]
+    b = fe.Batch([m for _, _, m in inst])
+    eb = b.rayleigh_ritz(Xs, prec=P)
+    for (om, V, m), X, Xs1, e in zip(inst, Xs, singles, eb):
+        es = m.rayleigh_ritz(Xs1, prec=P)
+        tol = 1e-10 if prec == "f64" else 1e-6 * float(torch.max(torch.abs(es)))
+        assert torch.max(torch.abs(e - es)) <= tol
+        Xd = X.double().cpu().numpy()
+        G = Xd.T @ Xd
+        assert np.max(np.abs(G - np.eye(nvec))) <= (1e-10 if prec == "f64" else 1e-5)
+        H = assembly.hamiltonian(om, V)
+        rq = np.einsum("ij,ij->j", Xd, H @ Xd)
+        assert np.max(np.abs(rq - e.cpu().numpy())) <= (1e-9 if prec == "f64" else 1e-4) * max(1.0, float(np.max(np.abs(rq))))
+
+
+def test_batch_rayleigh_ritz_needs_tensor_core_products_for_float(fe):
+    (om, V, m), = _instances(fe, [4], seed=2)
+    m.set_rr_products(False)
+    b = fe.Batch([m])
+    X = torch.zeros((om.n_psi, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(fe.FeError) as e:
+        b.rayleigh_ritz([X], prec=fe.FE_F32)
+    assert e.value.status == 7
