@@ -112,11 +112,11 @@ template <typename V>
 __global__ void k_psum(const V* __restrict__ x, const V* __restrict__ y, int64_t n,
                        double* __restrict__ part) {
   __shared__ double sh[fe::RED_THREADS];
-  double s = 0.0;
+  V s = V(0);   // a thread's few terms in the vector precision, the block sum in double
   for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
        i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS)
-    s += y ? (double)x[i] * (double)y[i] : (double)x[i];
-  sh[threadIdx.x] = s;
+    s += y ? x[i] * y[i] : x[i];
+  sh[threadIdx.x] = (double)s;
   __syncthreads();
   for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
@@ -176,19 +176,20 @@ __global__ void k_precond(V* __restrict__ r, V* __restrict__ z, const V* __restr
                           int64_t n, double* __restrict__ part_rz, double* __restrict__ part_rr,
                           const double* __restrict__ cy, int64_t plane) {
   __shared__ double sh1[fe::RED_THREADS], sh2[fe::RED_THREADS];
-  const double mean = project ? s->mean : 0.0;
-  double a1 = 0.0, a2 = 0.0;
+  const V mean = project ? (V)s->mean : V(0);
+  const uint32_t pl = (uint32_t)plane;
+  V a1 = V(0), a2 = V(0);
   for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
        i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS) {
     V ri = r[i];
-    if (project) { ri = (V)((double)ri - mean); r[i] = ri; }
-    const V zi = mask[i] ? V(0) : (V)((double)dinv[i] * (double)ri + (cy ? cy[i / plane] : 0.0));
+    if (project) { ri -= mean; r[i] = ri; }
+    const V zi = mask[i] ? V(0) : dinv[i] * ri + (cy ? (V)cy[(uint32_t)i / pl] : V(0));
     z[i] = zi;
-    a1 += (double)ri * (double)zi;
-    a2 += (double)ri * (double)ri;
+    a1 += ri * zi;
+    a2 += ri * ri;
   }
-  sh1[threadIdx.x] = a1;
-  sh2[threadIdx.x] = a2;
+  sh1[threadIdx.x] = (double)a1;
+  sh2[threadIdx.x] = (double)a2;
   __syncthreads();
   for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) { sh1[threadIdx.x] += sh1[threadIdx.x + w]; sh2[threadIdx.x] += sh2[threadIdx.x + w]; }
@@ -235,19 +236,19 @@ __global__ void k_update_xr(V* __restrict__ x, V* __restrict__ r, const V* __res
                             const V* __restrict__ q, const unsigned char* __restrict__ mask,
                             const CgState* s, int64_t n, double* __restrict__ part) {
   __shared__ double sh[fe::RED_THREADS];
-  const double a = s->alpha;
-  double acc = 0.0;
+  const V a = (V)s->alpha;
+  V acc = V(0);
   for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
        i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS) {
     V ri = r[i];
     if (!mask[i]) {
-      x[i] = (V)((double)x[i] + a * (double)p[i]);
-      ri = (V)((double)ri - a * (double)q[i]);
+      x[i] += a * p[i];
+      ri -= a * q[i];
       r[i] = ri;
     }
-    acc += (double)ri;
+    acc += ri;
   }
-  sh[threadIdx.x] = acc;
+  sh[threadIdx.x] = (double)acc;
   __syncthreads();
   for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
@@ -278,10 +279,10 @@ template <typename V>
 __global__ void k_update_p(V* __restrict__ p, const V* __restrict__ z, const CgState* s,
                            int64_t n) {
   if (s->done && s->alpha == 0.0) return;
-  const double b = s->beta;
+  const V b = (V)s->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = (V)((double)z[i] + b * (double)p[i]);
+    p[i] = z[i] + b * p[i];
 }
 
 // mixed-precision refinement: the float copy of the double residual, and phi += delta
@@ -356,12 +357,12 @@ __global__ void k_plane_sum(const V* __restrict__ x, const unsigned char* __rest
                             int64_t plane, double* __restrict__ out) {
   __shared__ double sh[fe::RED_THREADS];
   const int64_t base = (int64_t)blockIdx.x * plane;
-  double a = 0.0;
+  V a = V(0);
   for (int64_t i = threadIdx.x; i < plane; i += fe::RED_THREADS) {
     const int64_t id = base + i;
-    if (!mask[id]) a += x ? (double)x[id] : 1.0;
+    if (!mask[id]) a += x ? x[id] : V(1);
   }
-  sh[threadIdx.x] = a;
+  sh[threadIdx.x] = (double)a;
   __syncthreads();
   for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
@@ -779,6 +780,8 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
     return fe_fail(FE_EINVAL, "fe_poisson_solve: need zA < zB");
   FE_TRY(fe_activate(m));
   const int64_t n = m->n_phi;
+  if (n >= (int64_t(1) << 32))
+    return fe_fail(FE_EUNSUPPORTED, "fe_poisson_solve: 2^32 or more phi nodes");
   const int nzp = m->NZ;
   cudaStream_t st = m->stream;
   const bool mixed = m->poisson_arith == FE_POISSON_MIXED;
