@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--prec", choices=["f32", "f64", "bf16", "f32x3"], default="f32")
+    ap.add_argument("--prec", choices=["f32", "f64", "bf16"], default="f32")
     ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep"], default="p5",
                     help="p5: the benchmark slab; p5s / p3: smaller slabs; sweep: the batched "
                          "bias sweep of 24 independent 8x8xH-cell p=4 slabs")
@@ -294,9 +294,8 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = {"f32": fe.FE_F32, "f64": fe.FE_F64, "bf16": fe.FE_BF16_F32ACC,
-            "f32x3": fe.FE_F32_F32ACC}[args.prec]
-    dtype_name = {"f32": "f32", "f64": "f64", "bf16": "bf16", "f32x3": "f32"}[args.prec]
+    prec = {"f32": fe.FE_F32, "f64": fe.FE_F64, "bf16": fe.FE_BF16_F32ACC}[args.prec]
+    dtype_name = {"f32": "f32", "f64": "f64", "bf16": "bf16"}[args.prec]
     slab = workload(args.workload)
     nvec, degree = slab.nvec, slab.degree
     lib = fe.load()

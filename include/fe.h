@@ -61,8 +61,9 @@ typedef enum {
  *   FE_F32          float storage, float sum-factorised products, float accumulation.
  *   FE_BF16_F32ACC  float storage, per-cell dense stiffness products with bf16 operands
  *                   on the tcgen05 tensor cores, float accumulation in tensor memory.
- *   FE_F32_F32ACC   float storage, per-cell dense products with the float operands split
- *                   into bf16 high and low parts on tcgen05, float accumulation.        */
+ *   FE_F32_F32ACC   reserved for per-cell dense products with the float operands split
+ *                   into bf16 high and low parts on tcgen05; not built in this version:
+ *                   every entry point returns FE_EUNSUPPORTED for it.                    */
 typedef enum { FE_F64 = 0, FE_F32 = 1, FE_BF16_F32ACC = 2, FE_F32_F32ACC = 3 } fe_precision;
 
 /* Wavefunction boundary condition on a z face (x and y are always periodic). */
@@ -202,6 +203,34 @@ fe_status fe_batch_cheb_filter(fe_batch* batch, void* const* X, const int64_t* n
  * n x n work array. */
 fe_status fe_batch_rayleigh_ritz(fe_batch* batch, void* const* X, int64_t nvec,
                                  const int64_t* ld, double* const* eig, fe_precision prec);
+
+/* ---- self-consistent closure ------------------------------------------------------------
+ * Density of a block (Section 2.1, below Eq. Tsexc: rho = 2 sum_n f_n |psi_n|^2): the
+ * block holds xt_n = M^1/2 u_n (orthonormal columns of Ht, Section 2.3), so
+ * rho_dev[I] = sum_n occ_dev[n] X[I][n]^2 / M_II at psi nodes (occ = 2 f, device array of
+ * nvec doubles) and 0 on the planes without psi nodes; rho_dev is [n_phi] (phi order), so
+ * it feeds fe_poisson_solve directly.  FE_F64 and FE_F32 blocks, nvec <= 4096. */
+fe_status fe_density(fe_mesh* mesh, const void* X, int64_t nvec, int64_t ld,
+                     const double* occ_dev, double* rho_dev, fe_precision prec);
+
+/* Fermi-Dirac occupations at smearing temperature kT (host arrays): occ_host[i] =
+ * 2 / (1 + exp((eig[i] - mu)/kT)) with mu (bisection) such that sum occ = n_electrons
+ * (0 <= n_electrons <= 2 n).  The paper defers the smearing to earlier work; this is the
+ * reading used here.  Needs no GPU. */
+fe_status fe_occupations(const double* eig_host, int n, double n_electrons, double kT,
+                         double* occ_host, double* mu);
+
+/* Anderson / Pulay mixing of phi-node densities (D. G. Anderson 1965, P. Pulay 1980) with
+ * the lumped-mass inner product: with R = rho_out - rho_in and the differences dR_i,
+ * drho_i of the last `history` (0..16) steps, gamma minimises |R - sum gamma_i dR_i| and
+ * rho_in <- rho_in + alpha R - sum gamma_i (drho_i + alpha dR_i) (history 0: linear
+ * mixing).  The mixer owns (3 + 2 history) n_phi doubles on the mesh's device; calls run
+ * on the mesh's stream; resid_norm (host) gets |R| in the same inner product. */
+typedef struct fe_mixer fe_mixer;
+fe_status fe_mixer_create(fe_mesh* mesh, int history, double alpha, fe_mixer** out);
+fe_status fe_mixer_destroy(fe_mixer* mixer);
+fe_status fe_mixer_step(fe_mixer* mixer, double* rho_in_dev, const double* rho_out_dev,
+                        double* resid_norm);
 
 typedef enum { FE_BIAS_CEF = 0, FE_BIAS_CPD = 1 } fe_bias_kind;
 

@@ -32,7 +32,8 @@ EXPORTS = [
     "fe_rayleigh_ritz", "fe_atom_fields", "fe_energy", "fe_atom_fields_vjp",
     "fe_lanczos_bounds", "fe_kernel_launches", "fe_last_error",
     "fe_batch_create", "fe_batch_destroy", "fe_batch_apply_H", "fe_batch_cheb_filter",
-    "fe_batch_rayleigh_ritz",
+    "fe_batch_rayleigh_ritz", "fe_density", "fe_occupations", "fe_mixer_create",
+    "fe_mixer_destroy", "fe_mixer_step",
 ]
 
 
@@ -99,6 +100,11 @@ def load(path=LIB_PATH):
         "fe_batch_apply_H": ([P, P, P, P, P, I], I),
         "fe_batch_cheb_filter": ([P, P, P, P, I, P, P, P, I], I),
         "fe_batch_rayleigh_ritz": ([P, P, I64, P, P, I], I),
+        "fe_density": ([P, P, I64, I64, P, P, I], I),
+        "fe_occupations": ([P, I, D, D, P, C.POINTER(D)], I),
+        "fe_mixer_create": ([P, I, D, C.POINTER(C.c_void_p)], I),
+        "fe_mixer_destroy": ([P], I),
+        "fe_mixer_step": ([P, P, P, C.POINTER(D)], I),
         "fe_kernel_launches": ([], I64),
         "fe_last_error": ([], C.c_char_p),
     }

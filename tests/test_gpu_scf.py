@@ -1,0 +1,91 @@
+"""Self-consistent closure on the GPU against the oracle: the block density (FP64 and FP32
+blocks), Anderson mixing step by step, and whole Hartree-level self-consistent runs on a
+small CEF and a small CPD slab (same start block, same parameters; each side computes its
+own Lanczos bounds).
+
+Tolerances: density 1e-12 (FP64) / 1e-6 (FP32 block) relative; mixing 1e-12; the runs
+1e-7 on mu, the Ritz values and the density (the Poisson solves stop at 1e-12 and the
+Lanczos bounds agree to ~1e-10, which perturbs the filter interval slightly)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import assembly, scf
+from oracle.mesh import Mesh as OMesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fe():
+    import paper_2504_00998_gb300 as fe
+    fe.load()
+    return fe
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_density_matches_oracle(fe, prec):
+    from paper_2504_00998_gb300 import scf as fscf
+    P = fe.FE_F64 if prec == "f64" else fe.FE_F32
+    L, ncell, p = (4.0, 4.0, 9.0), (2, 2, 4), 3
+    for dirichlet in ((True, True), (False, True)):
+        om = OMesh(L, ncell, p, dirichlet)
+        m = fe.Mesh(L, ncell, p, dirichlet)
+        rng = np.random.default_rng(4)
+        X = rng.standard_normal((om.n_psi, 24))
+        if prec == "f32":
+            X = X.astype(np.float32).astype(np.float64)
+        occ = rng.uniform(0.0, 2.0, 24)
+        M = assembly.lumped_mass(om)
+        ref = scf.density_phi(X, occ, M, om.psi_to_phi())
+        Xg = torch.tensor(X, dtype=fe.storage_dtype(P), device="cuda")
+        got = fscf.density(m, Xg, occ, P).cpu().numpy()
+        tol = 1e-12 if prec == "f64" else 1e-6
+        assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("history", [0, 3])
+def test_mixer_matches_oracle(fe, history):
+    from paper_2504_00998_gb300 import scf as fscf
+    m = fe.Mesh((4.0, 4.0, 9.0), (2, 2, 4), 3)
+    w = m.lumped_mass().cpu().numpy()
+    mix_ref = scf.AndersonMixer(w, alpha=0.35, history=history)
+    mix = fscf.Mixer(m, history=history, alpha=0.35)
+    rng = np.random.default_rng(8)
+    x_ref = rng.standard_normal(m.n_phi)
+    x = torch.tensor(x_ref, device="cuda")
+    A = 0.05 * rng.standard_normal((m.n_phi, m.n_phi)) / np.sqrt(m.n_phi)
+    c = rng.standard_normal(m.n_phi)
+    for _ in range(7):
+        out_ref = A @ x_ref + c
+        x_ref, r_ref = mix_ref.step(x_ref, out_ref)
+        out = torch.tensor(A @ x.cpu().numpy() + c, device="cuda")
+        r = mix.step(x, out)
+        assert abs(r - r_ref) <= 1e-12 * max(1.0, r_ref)
+        assert np.max(np.abs(x.cpu().numpy() - x_ref)) <= 1e-12 * np.max(np.abs(x_ref))
+    mix.close()
+
+
+@pytest.mark.parametrize("kind", ["cef", "cpd"])
+def test_scf_run_matches_oracle(fe, kind):
+    from paper_2504_00998_gb300 import scf as fscf
+    bias = W.Bias("cef", field=0.01) if kind == "cef" else W.Bias("cpd", dV=0.02, zA=1.5, zB=12.5)
+    base = W.small_slab(ncell=(2, 2, 6), p=3, L=(4.0, 4.0, 14.0), natoms=4, seed=3, nvec=16,
+                        degree=8)
+    slab = W.Slab(base.name, base.L, base.ncell, base.p, base.R, base.Z, bias, nvec=16, degree=8,
+                  seed=base.seed)
+    X0 = W.start_block(slab).astype(np.float64)
+    iters = 8
+    ref = scf.scf_run(slab, X0, iters=iters)
+    m = fe.Mesh.from_slab(slab)
+    X = torch.tensor(X0, device="cuda")
+    out = fscf.scf_run(m, bias, float(np.sum(slab.Z)), X, iters=iters, degree=8, prec=fe.FE_F64)
+    assert abs(out["mu"] - ref["mu"]) <= 1e-7
+    assert np.max(np.abs(out["eig"] - ref["eig"])) <= 1e-7
+    rho = out["rho"].cpu().numpy()
+    assert np.max(np.abs(rho - ref["rho"])) <= 1e-7 * np.max(np.abs(ref["rho"]))
+    np.testing.assert_allclose(out["res"], ref["res"], rtol=1e-5)
+    # the density of the converging run keeps the electron count
+    M = ref["M"]
+    assert abs(float(M @ rho) - float(np.sum(slab.Z))) <= 1e-9 * float(np.sum(slab.Z))
