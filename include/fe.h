@@ -204,6 +204,18 @@ fe_status fe_batch_cheb_filter(fe_batch* batch, void* const* X, const int64_t* n
 fe_status fe_batch_rayleigh_ritz(fe_batch* batch, void* const* X, int64_t nvec,
                                  const int64_t* ld, double* const* eig, fe_precision prec);
 
+/* ---- analysis outputs (Section 3) ---------------------------------------------------------
+ * Per phi plane of a phi-node field f_dev [n_phi], out_dev [NZ] (NZ = nz p + 1 planes, in
+ * z order): FE_PLANAR_INTEGRAL gives int_{S_z} f dx dy (Section 3.3's rho0(z)),
+ * FE_PLANAR_AVERAGE gives (1/A_z) int_{S_z} f dx dy (V0_bare(z)); lumped (GLL) quadrature. */
+enum { FE_PLANAR_INTEGRAL = 0, FE_PLANAR_AVERAGE = 1 };
+fe_status fe_planar(fe_mesh* mesh, const double* f_dev, int mode, double* out_dev);
+
+/* Dipole moment about the domain centre (Section 3.1), mu_z = int (b + rho)(z - Lz/2):
+ * rho_dev [n_phi] or NULL for the atoms' model density; b from fe_set_atoms; mu_z on the
+ * host.  The polarisability of Section 3.1 is the slope of mu_z over two fields. */
+fe_status fe_dipole(fe_mesh* mesh, const double* rho_dev, double* mu_z);
+
 /* ---- self-consistent closure ------------------------------------------------------------
  * Density of a block (Section 2.1, below Eq. Tsexc: rho = 2 sum_n f_n |psi_n|^2): the
  * block holds xt_n = M^1/2 u_n (orthonormal columns of Ht, Section 2.3), so
@@ -257,6 +269,11 @@ typedef struct { int iters; double rel_residual; int status; } fe_solve_info;
  * Returns FE_ENOCONV if max_iter is reached first. */
 fe_status fe_poisson_solve(fe_mesh* mesh, const double* rho_dev, const fe_poisson_bc* bc,
                            double* phi_dev, double* vbare_dev, fe_solve_info* info);
+
+/* V_bare = phi + (V_loc - V_sm) + V_app on every phi node (Section 3.3; V_app of the bias
+ * for CEF, zero for CPD), out_dev [n_phi]. */
+fe_status fe_vbare_phi(fe_mesh* mesh, const double* phi_dev, const fe_poisson_bc* bc,
+                       double* out_dev);
 
 /* Same solve for a given load f_dev [n_phi] (K phi = f on the free nodes) instead of
  * 4 pi M (rho + b).  CPD / L-CPD: constrained nodes take phic_dev [n_phi] (read on the

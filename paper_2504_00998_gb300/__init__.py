@@ -89,6 +89,26 @@ class Mesh:
         call("fe_set_option", self._h, _lib.FE_OPT_POISSON_PRECOND,
              _lib.FE_PRECOND_JACOBI_PLANES if planes else _lib.FE_PRECOND_JACOBI)
 
+    def planar(self, f, average=False):
+        """Per phi plane: the planar integral (rho0) or average (V0) of a phi-node field."""
+        out = self._f64(self.ncell[2] * self.p + 1)
+        call("fe_planar", self._h, _ptr(f.contiguous()), 1 if average else 0, _ptr(out))
+        return out
+
+    def dipole(self, rho=None):
+        """mu_z = int (b + rho)(z - Lz/2) (rho None: the atoms' model density)."""
+        mu = C.c_double()
+        call("fe_dipole", self._h, _ptr(rho.contiguous() if rho is not None else None),
+             C.byref(mu))
+        return mu.value
+
+    def vbare_phi(self, phi, bias):
+        """V_bare = phi + V_loc - V_sm + V_app on every phi node."""
+        out = self._f64(self.n_phi)
+        bc = self.make_bc(bias)
+        call("fe_vbare_phi", self._h, _ptr(phi.contiguous()), C.byref(bc), _ptr(out))
+        return out
+
     def set_poisson_mixed(self, mixed):
         """Poisson arithmetic: double CG (False) or float corrections refined against the
         double residual (True, the default); both stop at the same double residual."""

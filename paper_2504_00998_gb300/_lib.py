@@ -33,7 +33,7 @@ EXPORTS = [
     "fe_lanczos_bounds", "fe_kernel_launches", "fe_last_error",
     "fe_batch_create", "fe_batch_destroy", "fe_batch_apply_H", "fe_batch_cheb_filter",
     "fe_batch_rayleigh_ritz", "fe_density", "fe_occupations", "fe_mixer_create",
-    "fe_mixer_destroy", "fe_mixer_step",
+    "fe_mixer_destroy", "fe_mixer_step", "fe_planar", "fe_dipole", "fe_vbare_phi",
 ]
 
 
@@ -105,6 +105,9 @@ def load(path=LIB_PATH):
         "fe_mixer_create": ([P, I, D, C.POINTER(C.c_void_p)], I),
         "fe_mixer_destroy": ([P], I),
         "fe_mixer_step": ([P, P, P, C.POINTER(D)], I),
+        "fe_planar": ([P, P, I, P], I),
+        "fe_dipole": ([P, P, C.POINTER(D)], I),
+        "fe_vbare_phi": ([P, P, C.POINTER(FePoissonBC), P], I),
         "fe_kernel_launches": ([], I64),
         "fe_last_error": ([], C.c_char_p),
     }

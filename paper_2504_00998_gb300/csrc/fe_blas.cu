@@ -44,6 +44,13 @@ fe_status dot_async(const double* x, const double* y, int64_t n, int64_t inc, do
   return FE_OK;
 }
 
+fe_status sum_async(const double* part, int n, double* out, cudaStream_t st) {
+  k_sum_partial<<<1, RED_BLOCKS, 0, st>>>(part, n, out); fe_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fe_fail(FE_ECUDA, "sum: %s", cudaGetErrorString(e));
+  return FE_OK;
+}
+
 }  // namespace fe
 
 fe_status fe_dot(fe_mesh* m, const double* x, const double* y, int64_t n, double* out_dev) {

@@ -609,6 +609,18 @@ extern "C" fe_status fe_poisson_constraints(fe_mesh* m, const fe_poisson_bc* bc,
   return FE_OK;
 }
 
+extern "C" fe_status fe_vbare_phi(fe_mesh* m, const double* phi, const fe_poisson_bc* bc,
+                                  double* out) {
+  if (!m || !phi || !bc || !out) return fe_fail(FE_EINVAL, "fe_vbare_phi: null argument");
+  if (!m->d_vlms) return fe_fail(FE_EINVAL, "fe_vbare_phi: call fe_set_atoms first");
+  FE_TRY(fe_activate(m));
+  k_vbare<<<fe::grid_for(m->n_phi), 256, 0, m->stream>>>(make_geom(m), phi, m->d_vlms, bc->field,
+                                                           bc->kind == FE_BIAS_CEF, 0, out,
+                                                           m->n_phi); fe_count_launch();
+  FE_CUDA(cudaGetLastError());
+  return FE_OK;
+}
+
 extern "C" fe_status fe_poisson_solve(fe_mesh* m, const double* rho, const fe_poisson_bc* bc,
                                       double* phi, double* vbare, fe_solve_info* info) {
   if (!m || !bc || !phi) return fe_fail(FE_EINVAL, "fe_poisson_solve: null argument");
