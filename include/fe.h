@@ -132,6 +132,17 @@ fe_status fe_lumped_mass(const fe_mesh* mesh, double* m_dev);
 fe_status fe_set_atoms(fe_mesh* mesh, int n, const double* R_host, const double* Z_host,
                        double sigma_b, double rc_loc, double sigma_rho);
 
+/* Nonlocal pseudopotential term (Eq. V_nloc) with synthetic projectors: per atom a one s
+ * and three p channels, g = exp(-|d|^2 / (2 sigma_a^2)), p_s = g, p_x = (d_x / sigma_a) g,
+ * p_y, p_z likewise (d = x - R_a over the periodic x/y images, cut at |d| <= rc), and
+ * coefficients D_host[a][4] (s, x, y, z).  With the lumped quadrature the scaled operator
+ * gains Ht_nloc = M^1/2 P D P^T M^1/2, applied inside every Ht X of fe_apply_H,
+ * fe_cheb_filter, fe_rayleigh_ritz and fe_lanczos_bounds (all precisions).  natoms = 0
+ * removes the term.  Arrays are host arrays and are copied.  A mesh carrying the term is
+ * refused by fe_batch_create and fe_cheb_filter_static (FE_EUNSUPPORTED). */
+fe_status fe_set_nonlocal(fe_mesh* mesh, int natoms, const double* R_host,
+                          const double* sigma_host, const double* D_host, double rc);
+
 /* V_eff at psi nodes, veff_dev[n_psi] (Eq. Veff and Hloc without exchange-correlation:
  * V_eff = phi + V_loc - V_sm + V_app).  Copied into the mesh. */
 fe_status fe_set_potential(fe_mesh* mesh, const double* veff_dev);

@@ -131,6 +131,13 @@ class Mesh:
         call("fe_set_atoms", self._h, int(Z.numel()), _ptr(R), _ptr(Z), float(sigma_b),
              float(rc_loc), float(sigma_rho))
 
+    def set_nonlocal(self, R, sigma, D, rc):
+        """Nonlocal term with synthetic s + p projectors (R [n][3], sigma [n], D [n][4])."""
+        R = torch.as_tensor(R, dtype=torch.float64).contiguous().cpu()
+        sg = torch.as_tensor(sigma, dtype=torch.float64).contiguous().cpu()
+        Dt = torch.as_tensor(D, dtype=torch.float64).contiguous().cpu()
+        call("fe_set_nonlocal", self._h, int(sg.numel()), _ptr(R), _ptr(sg), _ptr(Dt), float(rc))
+
     def set_potential(self, veff):
         assert veff.dtype == torch.float64 and veff.is_cuda and veff.numel() == self.n_psi
         call("fe_set_potential", self._h, _ptr(veff.contiguous()))

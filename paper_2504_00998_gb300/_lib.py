@@ -34,6 +34,7 @@ EXPORTS = [
     "fe_batch_create", "fe_batch_destroy", "fe_batch_apply_H", "fe_batch_cheb_filter",
     "fe_batch_rayleigh_ritz", "fe_density", "fe_occupations", "fe_mixer_create",
     "fe_mixer_destroy", "fe_mixer_step", "fe_planar", "fe_dipole", "fe_vbare_phi",
+    "fe_set_nonlocal",
 ]
 
 
@@ -108,6 +109,7 @@ def load(path=LIB_PATH):
         "fe_planar": ([P, P, I, P], I),
         "fe_dipole": ([P, P, C.POINTER(D)], I),
         "fe_vbare_phi": ([P, P, C.POINTER(FePoissonBC), P], I),
+        "fe_set_nonlocal": ([P, I, P, P, P, D], I),
         "fe_kernel_launches": ([], I64),
         "fe_last_error": ([], C.c_char_p),
     }

@@ -40,20 +40,22 @@ fe_status fe_tc_apply(fe_mesh* m, const float* X, float* Y, const float* Z, int6
                       int64_t ld, float alpha, float beta, float shift, fe_precision prec);
 
 // Y = alpha (Ht - shift) X + beta Z in the requested arithmetic.
+// (plus alpha Ht_nloc X when the mesh carries the nonlocal term)
 fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t nvec, int64_t ld,
                      double alpha, double beta, double shift, fe_precision prec) {
   if (prec == FE_F64) {
     KronIO<double> io{(const double*)X, ld, (double*)Y, ld, (const double*)Z, ld, m->d_veff,
                       nvec, alpha, beta, shift};
-    return fe::kron_f64(m->coefH, fe_geom(m, true), io, m->stream);
-  }
-  if (prec == FE_F32) {
+    FE_TRY(fe::kron_f64(m->coefH, fe_geom(m, true), io, m->stream));
+  } else if (prec == FE_F32) {
     KronIO<float> io{(const float*)X, ld, (float*)Y, ld, (const float*)Z, ld, m->d_veff_f,
                      nvec, (float)alpha, (float)beta, (float)shift};
-    return fe::kron_f32(m->coefH, fe_geom(m, true), io, m->stream);
+    FE_TRY(fe::kron_f32(m->coefH, fe_geom(m, true), io, m->stream));
+  } else {
+    FE_TRY(fe_tc_apply(m, (const float*)X, (float*)Y, (const float*)Z, nvec, ld, (float)alpha,
+                       (float)beta, (float)shift, prec));
   }
-  return fe_tc_apply(m, (const float*)X, (float*)Y, (const float*)Z, nvec, ld, (float)alpha,
-                     (float)beta, (float)shift, prec);
+  return fe_nonlocal_apply(m, X, Y, nvec, ld, alpha, prec == FE_F64);
 }
 
 extern "C" fe_status fe_apply_H(fe_mesh* m, const void* X, void* Y, int64_t nvec, int64_t ld,

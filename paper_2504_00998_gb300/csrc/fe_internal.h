@@ -13,7 +13,7 @@
 
 #define FE_MAXP 6
 #define FE_MAXN1 (FE_MAXP + 1)
-#define FE_NWS 12   // workspace slots of a mesh
+#define FE_NWS 13   // workspace slots of a mesh
 
 // ---- error state ------------------------------------------------------------------------
 fe_status fe_fail(fe_status st, const char* fmt, ...);
@@ -125,6 +125,21 @@ fe_status kron_batch_f32(const KronCoef& cf, int p, const KronInst<float>* d_ins
                          int64_t total_ctas, bool use_z, bool full, cudaStream_t st);
 }  // namespace fe
 
+// ---- nonlocal projector tables (fe_nonlocal.cu) --------------------------------------------
+struct FeNonlocal {
+  int natoms = 0, nnz = 0, ntouched = 0;
+  int* atom_ptr = nullptr;     // [natoms + 1] entries of each atom
+  int* ent_node = nullptr;     // [nnz] psi node of each entry
+  int* ent_atom = nullptr;     // [nnz]
+  double* ent_val = nullptr;   // [nnz][4] M^1/2 p_beta at the node
+  float* ent_val_f = nullptr;
+  double* D = nullptr;         // [natoms][4]
+  float* D_f = nullptr;
+  int* tn_node = nullptr;      // [ntouched] psi nodes carrying entries
+  int* tn_ptr = nullptr;       // [ntouched + 1]
+  int* tn_ent = nullptr;       // [nnz] entries in node order
+};
+
 // ---- the mesh ---------------------------------------------------------------------------
 struct fe_mesh {
   fe_mesh_desc desc;
@@ -168,6 +183,8 @@ struct fe_mesh {
   int poisson_precond = 1;
   // Poisson arithmetic: 0 double CG, 1 float corrections with double residuals
   int poisson_arith = 1;
+  FeNonlocal nl;            // nonlocal term (natoms == 0: none)
+
   // cached coarse-space inverse (WS_PCOARSE): valid for the constraint set of pc_key
   int pc_state = 0;          // 0 none, 1 valid, 2 not SPD (Jacobi only for this key)
   int pc_nz = 0;
@@ -184,11 +201,16 @@ struct fe_mesh {
 
 enum { WS_CHEB = 0, WS_RR_X = 1, WS_RR_HX = 2, WS_RR_SMALL = 3, WS_CG = 4, WS_RED = 5,
        WS_LANCZOS = 6, WS_TC = 7, WS_TC_IMG = 8, WS_YCELL = 9, WS_RR_TC32 = 10,
-       WS_PCOARSE = 11 };
+       WS_PCOARSE = 11, WS_NL = 12 };
 
 fe_status fe_ws(fe_mesh* m, int slot, size_t bytes, void** out);
 fe_status fe_activate(const fe_mesh* m);
 KronGeom fe_geom(const fe_mesh* m, bool psi);
+
+// nonlocal term -- fe_nonlocal.cu: Y += alpha Ht_nloc X; release of the tables
+fe_status fe_nonlocal_apply(fe_mesh* m, const void* X, void* Y, int64_t nvec, int64_t ld,
+                            double alpha, bool dbl);
+void fe_nonlocal_free(fe_mesh* m);
 
 // fields (potentials, densities) -- fe_fields.cu
 fe_status fe_fields_build(fe_mesh* m);

@@ -289,6 +289,7 @@ extern "C" fe_status fe_mesh_destroy(fe_mesh* m) {
   cudaSetDevice(m->device);
   cudaStreamSynchronize(m->stream);
   for (int i = 0; i < FE_NWS; ++i) if (m->ws[i]) cudaFree(m->ws[i]);
+  fe_nonlocal_free(m);
   if (m->tc_err_pinned) cudaFreeHost(m->tc_err_pinned);
   cudaFree(m->d_veff);
   cudaFree(m->d_veff_f);

@@ -65,6 +65,8 @@ extern "C" fe_status fe_cheb_filter_static(fe_mesh* m, void* X, int64_t nvec, in
   if (!(a0 < a && a < b)) return fe_fail(FE_EINVAL, "fe_cheb_filter_static: need a0 < a < b");
   if (!m->has_potential)
     return fe_fail(FE_EINVAL, "fe_cheb_filter_static: call fe_set_potential first");
+  if (m->nl.natoms > 0)
+    return fe_fail(FE_EUNSUPPORTED, "fe_cheb_filter_static: the nonlocal term needs a workspace");
   const unsigned long long need = (unsigned long long)m->n_psi * (unsigned long long)ld * eb;
   if (need > FE_STATIC_SCRATCH_BYTES)
     return fe_fail(FE_EINVAL,
