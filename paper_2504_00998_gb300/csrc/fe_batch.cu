@@ -429,6 +429,7 @@ extern "C" fe_status fe_batch_rayleigh_ritz(fe_batch* b, void* const* X, int64_t
   FE_CUDA(cudaMemcpyAsync(pS, hS.data(), sizeof(double*) * nb, cudaMemcpyHostToDevice, st));
   FE_CUDA(cudaMemcpyAsync(pH, hH.data(), sizeof(double*) * nb, cudaMemcpyHostToDevice, st));
 
+  FiniteEmulationGuard finite(m0->cublas);
   // block products
   for (int i = 0; i < nb; ++i) {
     const int N = (int)b->meshes[i]->n_psi;

@@ -52,6 +52,23 @@ void fe_count_launch(int64_t n = 1);
     if (t_ != FE_OK) return t_;       \
   } while (0)
 
+// ---- cuBLAS's FP32-accurate BF16x9 emulation on finite blocks ----------------------------
+// The Rayleigh-Ritz products of float blocks run as BF16x9 emulated GEMMs.  By default cuBLAS
+// first scans both operands for infinities and NaNs; the blocks here are finite, so the
+// guard turns that scan off for its lifetime and restores the previous setting after.
+struct FiniteEmulationGuard {
+  cublasHandle_t h;
+  cudaEmulationSpecialValuesSupport old = CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_DEFAULT;
+  explicit FiniteEmulationGuard(cublasHandle_t handle) : h(handle) {
+    if (cublasGetEmulationSpecialValuesSupport(h, &old) != CUBLAS_STATUS_SUCCESS)
+      old = CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_DEFAULT;
+    cublasSetEmulationSpecialValuesSupport(h, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
+  }
+  ~FiniteEmulationGuard() { cublasSetEmulationSpecialValuesSupport(h, old); }
+  FiniteEmulationGuard(const FiniteEmulationGuard&) = delete;
+  FiniteEmulationGuard& operator=(const FiniteEmulationGuard&) = delete;
+};
+
 // ---- tensor-product operator arguments ----------------------------------------------------
 // The assembled stiffness of the tensor-product mesh is
 //   K = ax K1 (x) M1 (x) M1 + ay M1 (x) K1 (x) M1 + az M1 (x) M1 (x) K1   (x (x) y (x) z),

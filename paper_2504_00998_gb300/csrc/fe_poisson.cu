@@ -170,13 +170,18 @@ __global__ void k_fin_mean(const double* part, CgState* s, double inv_n) {
 
 // r -= mean (CEF only); z = Dinv r (+ the coarse correction of the node's plane) on free
 // rows; one partial of r.z and r.r per block (of the stored, possibly rounded, values)
+// (mean_part: the block partials of sum r, reduced here by every block instead of a separate
+// finishing kernel; nullptr: the mean already in the state)
 template <typename V>
 __global__ void k_precond(V* __restrict__ r, V* __restrict__ z, const V* __restrict__ dinv,
                           const unsigned char* __restrict__ mask, const CgState* s, int project,
                           int64_t n, double* __restrict__ part_rz, double* __restrict__ part_rr,
-                          const double* __restrict__ cy, int64_t plane) {
+                          const double* __restrict__ cy, int64_t plane,
+                          const double* __restrict__ mean_part) {
   __shared__ double sh1[fe::RED_THREADS], sh2[fe::RED_THREADS];
-  const V mean = project ? (V)s->mean : V(0);
+  double mean_d = 0.0;
+  if (project) mean_d = mean_part ? block_sum_partials(mean_part) * (1.0 / (double)n) : s->mean;
+  const V mean = (V)mean_d;
   const uint32_t pl = (uint32_t)plane;
   V a1 = V(0), a2 = V(0);
   for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
@@ -231,12 +236,21 @@ __global__ void k_fin_alpha(const double* part, CgState* s) {
 }
 
 // x += alpha p; r -= alpha q (free rows); partial sums of r for the projection
+// (pq_part: the block partials of p.q; every block forms alpha = r.z / p.q itself and block 0
+// records it in the state, so no separate finishing kernel runs)
 template <typename V>
 __global__ void k_update_xr(V* __restrict__ x, V* __restrict__ r, const V* __restrict__ p,
                             const V* __restrict__ q, const unsigned char* __restrict__ mask,
-                            const CgState* s, int64_t n, double* __restrict__ part) {
+                            CgState* s, int64_t n, double* __restrict__ part,
+                            const double* __restrict__ pq_part) {
   __shared__ double sh[fe::RED_THREADS];
-  const V a = (V)s->alpha;
+  const double pq = block_sum_partials(pq_part);
+  const double al = (s->done || pq == 0.0) ? 0.0 : s->rz / pq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    s->pq = pq;
+    s->alpha = al;
+  }
+  const V a = (V)al;
   V acc = V(0);
   for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
        i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS) {
@@ -385,10 +399,12 @@ constexpr int COARSE_COLS = 64;   // coarse unknowns per block of k_coarse_apply
 // dense [nz][nz]; block b computes y[64 b, 64 b + 64) with four k-slices per column
 __global__ void k_coarse_apply(const double* __restrict__ sums, const double* __restrict__ cnt,
                                const double* __restrict__ Ainv, const CgState* st, int project,
-                               int nz, double* __restrict__ y) {
+                               int nz, double* __restrict__ y, const double* __restrict__ mean_part,
+                               double inv_n) {
   extern __shared__ double cb[];                    // b[nz], then partials [4][64]
   double* part = cb + nz;
-  const double mean = project ? st->mean : 0.0;
+  double mean = 0.0;
+  if (project) mean = mean_part ? block_sum_partials(mean_part) * inv_n : st->mean;
   for (int k = threadIdx.x; k < nz; k += blockDim.x) cb[k] = sums[k] - mean * cnt[k];
   __syncthreads();
   const int jl = threadIdx.x % COARSE_COLS, ks = threadIdx.x / COARSE_COLS;
@@ -678,11 +694,12 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
   const int gb = fe::grid_for(n);
   const int cblocks = (nzp + COARSE_COLS - 1) / COARSE_COLS;
   const size_t csmem = sizeof(double) * ((size_t)nzp + 4 * COARSE_COLS);
-  auto coarse = [&]() {
+  auto coarse = [&](const double* mean_part) {
     if (!b.Ainv) return;
     k_plane_sum<V><<<nzp, fe::RED_THREADS, 0, st>>>(b.r, b.mask, plane, b.csum); fe_count_launch();
     k_coarse_apply<<<cblocks, 4 * COARSE_COLS, csmem, st>>>(b.csum, b.ccnt, b.Ainv, b.s, project,
-                                                            nzp, b.cy); fe_count_launch();
+                                                            nzp, b.cy, mean_part, 1.0 / (double)n);
+    fe_count_launch();
   };
   const double* cy = b.Ainv ? b.cy : nullptr;
   CgState s0 = {};
@@ -692,9 +709,9 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
     k_psum<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, nullptr, n, b.pa); fe_count_launch();
     k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(b.pa, b.s, 1.0 / (double)n); fe_count_launch();
   }
-  coarse();
+  coarse(nullptr);
   k_precond<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project, n,
-                                                           b.pc, b.pd, cy, plane); fe_count_launch();
+                                                           b.pc, b.pd, cy, plane, nullptr); fe_count_launch();
   k_fin_init<<<1, fe::RED_BLOCKS, 0, st>>>(b.pc, b.pd, b.s, rtol, tol2_abs); fe_count_launch();
   k_copy<V><<<gb, 256, 0, st>>>(b.z, b.p, n); fe_count_launch();
   FE_CUDA(cudaGetLastError());
@@ -702,13 +719,12 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
   auto iteration = [&]() -> fe_status {
     FE_TRY(apply_K_v(m, b.p, b.q));
     k_psum<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.p, b.q, n, b.pa); fe_count_launch();
-    k_fin_alpha<<<1, fe::RED_BLOCKS, 0, st>>>(b.pa, b.s); fe_count_launch();
     k_update_xr<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.x, b.r, b.p, b.q, b.mask, b.s, n,
-                                                               b.pb); fe_count_launch();
-    if (project) { k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(b.pb, b.s, 1.0 / (double)n); fe_count_launch(); }
-    coarse();
+                                                               b.pb, b.pa); fe_count_launch();
+    coarse(b.pb);
     k_precond<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project,
-                                                             n, b.pc, b.pd, cy, plane); fe_count_launch();
+                                                             n, b.pc, b.pd, cy, plane, b.pb);
+    fe_count_launch();
     k_fin_beta<<<1, fe::RED_BLOCKS, 0, st>>>(b.pc, b.pd, b.s); fe_count_launch();
     k_update_p<V><<<gb, 256, 0, st>>>(b.p, b.z, b.s, n); fe_count_launch();
     return FE_OK;
@@ -742,9 +758,10 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
       k_psum<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, nullptr, n, b.pa); fe_count_launch();
       k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(b.pa, b.s, 1.0 / (double)n); fe_count_launch();
     }
-    coarse();
+    coarse(nullptr);
     k_precond<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project,
-                                                             n, b.pc, b.pd, cy, plane); fe_count_launch();
+                                                             n, b.pc, b.pd, cy, plane, nullptr);
+    fe_count_launch();
     k_fin_replace<<<1, fe::RED_BLOCKS, 0, st>>>(b.pc, b.pd, b.s); fe_count_launch();
     if (restart) { k_copy<V><<<gb, 256, 0, st>>>(b.z, b.p, n); fe_count_launch(); }
   };

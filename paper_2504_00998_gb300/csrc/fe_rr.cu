@@ -249,6 +249,7 @@ fe_status rr_gram_path_tc32(fe_mesh* m, float* X, int64_t ld, const float* HX, i
   float* Sf = (float*)sp;
   float* Hf = Sf + (size_t)n * n;
   const cublasComputeType_t ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+  FiniteEmulationGuard finite(m->cublas);
   FE_CUBLAS(cublasGemmEx(m->cublas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, N, &one, X, CUDA_R_32F,
                          (int)ld, X, CUDA_R_32F, (int)ld, &zero, Sf, CUDA_R_32F, n, ct,
                          CUBLAS_GEMM_DEFAULT));
