@@ -94,9 +94,11 @@ inline KronCoefT<T> convert_coef(const KronCoef& c) {
 }
 
 // A chunk is CH consecutive vector entries of one node: 16 bytes (float4 / double2) or,
-// for single-vector operators, one double.
+// for single-vector operators, one element.  Aligned to its size so that every shared- and
+// global-memory access of a chunk is one vector instruction (the block layouts guarantee
+// it: 16-byte aligned blocks whose rows are a multiple of 16 bytes).
 template <typename T, int CH>
-struct Chunk {
+struct alignas(sizeof(T) * CH) Chunk {
   T v[CH];
   __device__ __forceinline__ void zero() {
 #pragma unroll
@@ -112,6 +114,18 @@ struct Chunk {
 template <>
 __device__ __forceinline__ float Chunk<float, 4>::fma_t(float a, float b, float c) {
   return __fmaf_rn(a, b, c);
+}
+// d0,d1 += c * (b0,b1): one paired FP32 FMA (the same correctly rounded fma in each lane)
+__device__ __forceinline__ void ffma2(float& d0, float& d1, float c, float b0, float b1) {
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %2};\n\tmov.b64 rb, {%3, %4};\n\t"
+      "mov.b64 rd, {%0, %1};\n\tfma.rn.f32x2 rd, ra, rb, rd;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "+f"(d0), "+f"(d1) : "f"(c), "f"(b0), "f"(b1));
+}
+// float chunks accumulate two lanes per instruction
+template <>
+__device__ __forceinline__ void Chunk<float, 4>::fma(float a, const Chunk& x) {
+  ffma2(v[0], v[1], a, x.v[0], x.v[1]);
+  ffma2(v[2], v[3], a, x.v[2], x.v[3]);
 }
 template <>
 __device__ __forceinline__ double Chunk<double, 2>::fma_t(double a, double b, double c) {
@@ -548,8 +562,15 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
 // 1D grid, vector tile fastest: the CTAs that read the other halves of a node's DRAM
 // bursts (neighbouring vector tiles of the same xy block) run side by side, so a burst is
 // fetched once; neighbouring xy blocks (halo sharing) follow within the resident window.
+// Residency bound: the float operator's tiles of up to 256 threads are held to three CTAs per
+// SM (at most 85 registers), where the per-plane barriers of one CTA overlap two others' work.
+template <typename T, int CH, class TL>
+struct KronMinBlocks {
+  static constexpr int value = (std::is_same<T, float>::value && CH == 4 && TL::NTHR <= 256) ? 3 : 1;
+};
+
 template <typename T, int CH, class TL, bool FULL>
-__global__ void __launch_bounds__(TL::NTHR)
+__global__ void __launch_bounds__(TL::NTHR, (KronMinBlocks<T, CH, TL>::value))
 kron_kernel(const KronCoefT<T> cf, const KronGeom g, const KronIO<T> io, int nvt) {
   const int b = blockIdx.x;
   const int nxy = g.nbx * g.nby;
@@ -561,7 +582,7 @@ kron_kernel(const KronCoefT<T> cf, const KronGeom g, const KronIO<T> io, int nvt
 // table) in one launch.  The 1D grid concatenates the instances' CTA grids; a CTA finds its
 // instance by binary search over the ascending first-CTA offsets.
 template <typename T, int CH, class TL, bool FULL>
-__global__ void __launch_bounds__(TL::NTHR)
+__global__ void __launch_bounds__(TL::NTHR, (KronMinBlocks<T, CH, TL>::value))
 kron_batch_kernel(const KronCoefT<T> cf, const KronInst<T>* __restrict__ inst, int ninst) {
   const int64_t b = blockIdx.x;
   int lo = 0, hi = ninst - 1;
