@@ -304,6 +304,13 @@ fe_status fe_poisson_constraints(fe_mesh* mesh, const fe_poisson_bc* bc, unsigne
 /* y = K x on phi nodes (Section 2.3), x, y [n_phi] doubles; no constraints applied. */
 fe_status fe_poisson_apply_K(fe_mesh* mesh, const double* x_dev, double* y_dev);
 
+/* The same product in float, x, y [n_phi] floats (distinct arrays, 4-byte aligned): the
+ * operator of the float Poisson iterations.  Formed cell by cell (sum-factorised cell
+ * products into a mesh-owned scratch of (p+1)^3 floats per cell, allocated on first use, then
+ * a per-node sum of the cell copies in a fixed order), so repeated calls give identical bits.
+ * FE_EINVAL for null or aliased arrays, FE_ENOMEM if the scratch cannot be allocated. */
+fe_status fe_poisson_apply_K_f32(fe_mesh* mesh, const float* x_dev, float* y_dev);
+
 /* Poisson load 4 pi M (rho + b) at phi nodes [n_phi] for the atoms (rho_dev NULL) or the
  * given density; f_dev [n_phi]; rho_out_dev / b_out_dev optional [n_phi] copies. */
 fe_status fe_poisson_rhs(fe_mesh* mesh, const double* rho_dev, double* f_dev,

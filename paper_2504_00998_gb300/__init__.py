@@ -167,8 +167,10 @@ class Mesh:
         return lo.value, hi.value
 
     def poisson_apply_K(self, x, y=None):
+        """y = K x; float64 through fe_poisson_apply_K, float32 through fe_poisson_apply_K_f32."""
         y = torch.empty_like(x) if y is None else y
-        call("fe_poisson_apply_K", self._h, _ptr(x), _ptr(y))
+        name = "fe_poisson_apply_K_f32" if x.dtype == torch.float32 else "fe_poisson_apply_K"
+        call(name, self._h, _ptr(x), _ptr(y))
         return y
 
     def poisson_rhs(self, rho=None):

@@ -28,7 +28,7 @@ EXPORTS = [
     "fe_lumped_mass", "fe_set_atoms", "fe_set_potential", "fe_apply_H", "fe_cheb_filter",
     "fe_cheb_filter_static",
     "fe_poisson_solve", "fe_poisson_solve_load", "fe_poisson_constraints",
-    "fe_poisson_apply_K", "fe_poisson_rhs",
+    "fe_poisson_apply_K", "fe_poisson_apply_K_f32", "fe_poisson_rhs",
     "fe_rayleigh_ritz", "fe_atom_fields", "fe_energy", "fe_atom_fields_vjp",
     "fe_lanczos_bounds", "fe_kernel_launches", "fe_last_error",
     "fe_batch_create", "fe_batch_destroy", "fe_batch_apply_H", "fe_batch_cheb_filter",
@@ -89,6 +89,7 @@ def load(path=LIB_PATH):
         "fe_poisson_solve_load": ([P, P, C.POINTER(FePoissonBC), P, P, C.POINTER(FeSolveInfo)], I),
         "fe_poisson_constraints": ([P, C.POINTER(FePoissonBC), P, P], I),
         "fe_poisson_apply_K": ([P, P, P], I),
+        "fe_poisson_apply_K_f32": ([P, P, P], I),
         "fe_poisson_rhs": ([P, P, P, P, P], I),
         "fe_rayleigh_ritz": ([P, P, I64, I64, P, I], I),
         "fe_lanczos_bounds": ([P, P, I, C.POINTER(D), C.POINTER(D)], I),

@@ -117,6 +117,15 @@ extern "C" fe_status fe_poisson_apply_K(fe_mesh* m, const double* x, double* y) 
   return fe::kron_k1(m->coefK, fe_geom(m, false), io, m->stream);
 }
 
+extern "C" fe_status fe_poisson_apply_K_f32(fe_mesh* m, const float* x, float* y) {
+  if (!m || !x || !y) return fe_fail(FE_EINVAL, "fe_poisson_apply_K_f32: null argument");
+  if (((uintptr_t)x) % 4 || ((uintptr_t)y) % 4)
+    return fe_fail(FE_EINVAL, "fe_poisson_apply_K_f32: arrays must be 4-byte aligned");
+  if (x == y) return fe_fail(FE_EINVAL, "fe_poisson_apply_K_f32: x and y must differ");
+  FE_TRY(fe_activate(m));
+  return fe_kcell_apply_f32(m, x, y);
+}
+
 // ---- Lanczos ---------------------------------------------------------------------------------
 namespace {
 

@@ -13,7 +13,7 @@
 
 #define FE_MAXP 6
 #define FE_MAXN1 (FE_MAXP + 1)
-#define FE_NWS 13   // workspace slots of a mesh
+#define FE_NWS 14   // workspace slots of a mesh
 
 // ---- error state ------------------------------------------------------------------------
 fe_status fe_fail(fe_status st, const char* fmt, ...);
@@ -218,9 +218,13 @@ struct fe_mesh {
 
 enum { WS_CHEB = 0, WS_RR_X = 1, WS_RR_HX = 2, WS_RR_SMALL = 3, WS_CG = 4, WS_RED = 5,
        WS_LANCZOS = 6, WS_TC = 7, WS_TC_IMG = 8, WS_YCELL = 9, WS_RR_TC32 = 10,
-       WS_PCOARSE = 11, WS_NL = 12 };
+       WS_PCOARSE = 11, WS_NL = 12, WS_KCELL = 13 };
 
 fe_status fe_ws(fe_mesh* m, int slot, size_t bytes, void** out);
+// single-vector float stiffness product through cell-local products (fe_kcell.cu); its
+// scratch (WS_KCELL) is fe_kcell_scratch_bytes
+size_t fe_kcell_scratch_bytes(const fe_mesh* m);
+fe_status fe_kcell_apply_f32(fe_mesh* m, const float* x, float* y);
 fe_status fe_activate(const fe_mesh* m);
 KronGeom fe_geom(const fe_mesh* m, bool psi);
 

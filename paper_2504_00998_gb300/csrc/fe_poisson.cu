@@ -17,6 +17,7 @@
 // host reads the convergence flag between replays.  The iteration cap bounds the loop.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -667,10 +668,7 @@ struct CgBuf {
 };
 
 fe_status apply_K_v(fe_mesh* m, const double* x, double* y) { return fe_poisson_apply_K(m, x, y); }
-fe_status apply_K_v(fe_mesh* m, const float* x, float* y) {
-  KronIO<float> io{x, 1, y, 1, nullptr, 1, nullptr, 1, 1.0f, 0.0f, 0.0f};
-  return fe::kron_k1f(m->coefK, fe_geom(m, false), io, m->stream);
-}
+fe_status apply_K_v(fe_mesh* m, const float* x, float* y) { return fe_kcell_apply_f32(m, x, y); }
 
 // CG on K_ff x = r0 from the iterate in b.x, whose masked residual is in b.r (projected by
 // the first preconditioner call for CEF).  Stops at |r|^2 <= tol2_abs, or (tol2_abs <= 0)
@@ -687,6 +685,11 @@ template <typename V, typename Hook>
 fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double tol2_abs,
                  int maxit, bool use_graph, cudaGraphExec_t* exec, int64_t* graph_kernels,
                  CgState* out, Hook&& hook) {
+  if constexpr (std::is_same<V, float>::value) {
+    // the float operator's scratch exists before any graph capture
+    void* w = nullptr;
+    FE_TRY(fe_ws(m, WS_KCELL, fe_kcell_scratch_bytes(m), &w));
+  }
   const int64_t n = m->n_phi;
   const int64_t plane = (int64_t)m->NX * m->NY;
   const int nzp = m->NZ;
@@ -902,9 +905,22 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
     FE_CUDA(cudaMemsetAsync(df, 0, sizeof(float) * n, st));
     CgBuf<float> bf{df, rf, zf, pf, qf, dinvf, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv};
     double rr_last = rr;
-    int it_last = 0, stalls = 0;
+    int it_last = 0, stalls = 0, breakdowns = 0;
     auto reliable = [&](const CgState& cs, int* action) -> fe_status {
       used = cs.iters;
+      // A kept search direction that no longer matches the replaced residual can make the
+      // float recurrence grow without bound (seen far below float resolution of the
+      // original load).  Its correction since the last replacement is then discarded (phi
+      // and the double residual r are those of that replacement) and the iteration
+      // restarts from r; a second breakdown hands the solve to the double CG.
+      if (!(cs.rr <= 1e2 * rr_last)) {
+        FE_CUDA(cudaMemsetAsync(df, 0, sizeof(float) * n, st));
+        if (++breakdowns >= 2 || cs.iters >= bc->max_iter) { *action = CG_STOP; return FE_OK; }
+        it_last = cs.iters;
+        k_to_float<<<gb, 256, 0, st>>>(r, rf, n); fe_count_launch();
+        *action = CG_RESTARTED;
+        return FE_OK;
+      }
       const bool trigger = cs.done || cs.rr <= 1e-4 * rr_last || cs.iters - it_last >= 512;
       if (!trigger) { *action = CG_CONTINUE; return FE_OK; }
       k_add_delta<<<gb, 256, 0, st>>>(phi, df, mask, n); fe_count_launch();

@@ -49,6 +49,32 @@ def test_apply_K_matches_oracle(fe, L, ncell, p):
     np.testing.assert_allclose(m.node_coords().cpu().numpy(), om.phi_coords(), atol=1e-13)
 
 
+@pytest.mark.parametrize("L,ncell,p", [((4.0, 4.0, 9.0), (2, 2, 4), 3), ((3.0, 5.0, 7.0), (3, 1, 3), 2),
+                                       ((6.0, 6.0, 6.0), (2, 2, 2), 6), ((2.0, 2.0, 4.0), (1, 1, 2), 1),
+                                       ((18.0, 4.0, 6.0), (9, 2, 3), 5), ((34.0, 2.0, 4.0), (17, 1, 2), 3),
+                                       ((10.0, 6.0, 8.0), (5, 3, 4), 6), ((70.0, 2.0, 4.0), (35, 1, 2), 1),
+                                       ((12.0, 12.0, 20.0), (6, 6, 10), 4)])
+def test_apply_K_f32_matches_oracle(fe, L, ncell, p):
+    """Float K x through the cell-local products (strips of 4 to 32 cells along x, so these
+    meshes include partial strips and one-cell periodic directions):
+    against the oracle's assembled K on the float-rounded input, 1e-5 relative (float
+    accumulation of at most 8 cell contributions of (p+1)-term products); two calls agree
+    bit for bit; the float entry rejects aliased arrays."""
+    om = OMesh(L, ncell, p)
+    K = assembly.assemble_stiffness(om)
+    m = fe.Mesh(L, ncell, p)
+    x = np.random.default_rng(1).standard_normal(om.n_phi).astype(np.float32)
+    xt = torch.tensor(x, device="cuda")
+    y1 = m.poisson_apply_K(xt)
+    y2 = m.poisson_apply_K(xt)
+    assert torch.equal(y1, y2)
+    ref = K @ x.astype(np.float64)
+    got = y1.double().cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
+    with pytest.raises(fe.FeError):
+        fe._lib.call("fe_poisson_apply_K_f32", m.handle, fe._ptr(xt), fe._ptr(xt))
+
+
 def test_fields_and_load_match_oracle(fe):
     slab = W.small_slab(ncell=(3, 2, 4), p=3, L=(6.0, 4.0, 12.0), natoms=4, seed=11)
     om, K, M, X = _oracle(slab)
