@@ -42,15 +42,15 @@ k_cell_apply(const CellCoef cf, const float* __restrict__ x, float* __restrict__
   using S = CellStrip<P>;
   constexpr int N1 = S::N1, CX = S::CX, UW = S::UW;
   __shared__ float U[N1 * N1 * UW];               // [lz][ly][xl]
-  __shared__ float A[N1 * N1 * CX * N1];          // [lz][ly][c][lx]: y contraction with M1
-  __shared__ float B[N1 * N1 * CX * N1];          //                  y contraction with ay K1
-  __shared__ float W1[N1 * N1 * CX * N1];         // x contraction: M1 A
-  __shared__ float W2[N1 * N1 * CX * N1];         //                ax K1 A + M1 B
-  const int nstrip = (nx + CX - 1) / CX;
-  const int sx = blockIdx.x % nstrip;
-  const int cy = (blockIdx.x / nstrip) % ny;
-  const int cz = blockIdx.x / (nstrip * ny);
-  const int cx0 = sx * CX;
+  // [lz][ly][c][lx]: the y contractions with M1 (A) and ay K1 (B), then in place the x
+  // contractions W1 = M1 A (in A) and W2 = ax K1 A + M1 B (in B): an x line is read whole by
+  // the one thread that overwrites it
+  __shared__ float A[N1 * N1 * CX * N1];
+  __shared__ float B[N1 * N1 * CX * N1];
+  float* W1 = A;
+  float* W2 = B;
+  const int cy = blockIdx.y, cz = blockIdx.z;
+  const int cx0 = blockIdx.x * CX;
   const int tid = threadIdx.x;
   const int64_t plane = (int64_t)NX * NY;
 
@@ -135,40 +135,42 @@ k_cell_apply(const CellCoef cf, const float* __restrict__ x, float* __restrict__
   }
 }
 
-// y at node (gx, gy, gz) = sum of its copies in the discontinuous grid
-__global__ void k_cell_gather(const float* __restrict__ ycell, float* __restrict__ y, int p,
-                              int nx, int ny, int nz, int NX, int NY, int64_t n) {
-  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (id >= n) return;
-  const int64_t plane = (int64_t)NX * NY;
-  const int gz = (int)(id / plane);
-  const int rem = (int)(id - (int64_t)gz * plane);
-  const int gy = rem / NX, gx = rem - gy * NX;
-  const int n1 = p + 1;
-  // candidate discontinuous indices per direction: (cell, local) pairs, lower cell first
-  int dx[2], dy[2], dz[2];
-  int nxc = 0, nyc = 0, nzc = 0;
+// y at node (gx, gy, gz) = sum of its copies in the discontinuous grid; blocks of 32 x 8
+// nodes of one plane (blockIdx.z strides over the planes)
+template <int P>
+__global__ void __launch_bounds__(256)
+k_cell_gather(const float* __restrict__ ycell, float* __restrict__ y, int nx, int ny, int nz,
+              int NX, int NY) {
+  constexpr int N1 = P + 1;
+  const int gx = blockIdx.x * 32 + threadIdx.x;
+  const int gy = blockIdx.y * 8 + threadIdx.y;
+  if (gx >= NX || gy >= NY) return;
+  // the (cell, local index) copies of the node per direction, lower cell first
+  int dx[2], dy[2], nxc = 0, nyc = 0;
   {
-    const int c = gx / p, l = gx - c * p;
-    if (l == 0) dx[nxc++] = (c == 0 ? nx - 1 : c - 1) * n1 + p;
-    dx[nxc++] = c * n1 + l;
+    const int c = gx / P, l = gx - c * P;
+    if (l == 0) dx[nxc++] = (c == 0 ? nx - 1 : c - 1) * N1 + P;
+    dx[nxc++] = c * N1 + l;
   }
   {
-    const int c = gy / p, l = gy - c * p;
-    if (l == 0) dy[nyc++] = (c == 0 ? ny - 1 : c - 1) * n1 + p;
-    dy[nyc++] = c * n1 + l;
+    const int c = gy / P, l = gy - c * P;
+    if (l == 0) dy[nyc++] = (c == 0 ? ny - 1 : c - 1) * N1 + P;
+    dy[nyc++] = c * N1 + l;
   }
-  {
-    const int c = gz / p, l = gz - c * p;
-    if (l == 0 && c > 0) dz[nzc++] = (c - 1) * n1 + p;
-    if (c < nz) dz[nzc++] = c * n1 + l;
+  const int64_t dnx = (int64_t)nx * N1, dny = (int64_t)ny * N1;
+  for (int gz = blockIdx.z; gz <= nz * P; gz += gridDim.z) {
+    int dz[2], nzc = 0;
+    const int c = gz / P, l = gz - c * P;
+    if (l == 0 && c > 0) dz[nzc++] = (c - 1) * N1 + P;
+    if (c < nz) dz[nzc++] = c * N1 + l;
+    float s = 0.f;
+    for (int a = 0; a < nzc; ++a)
+      for (int b = 0; b < nyc; ++b) {
+        const float* row = ycell + ((int64_t)dz[a] * dny + dy[b]) * dnx;
+        for (int e = 0; e < nxc; ++e) s += row[dx[e]];
+      }
+    y[((int64_t)gz * NY + gy) * NX + gx] = s;
   }
-  const int64_t dnx = (int64_t)nx * n1, dny = (int64_t)ny * n1;
-  float s = 0.f;
-  for (int a = 0; a < nzc; ++a)
-    for (int b = 0; b < nyc; ++b)
-      for (int c = 0; c < nxc; ++c) s += ycell[((int64_t)dz[a] * dny + dy[b]) * dnx + dx[c]];
-  y[id] = s;
 }
 
 template <int P>
@@ -176,14 +178,13 @@ fe_status cell_apply_p(const CellCoef& cf, const fe_mesh* m, const float* x, flo
                        float* ycell) {
   using S = CellStrip<P>;
   const int nstrip = (m->nx + S::CX - 1) / S::CX;
-  const int64_t grid = (int64_t)nstrip * m->ny * m->nz;
-  if (grid > 0x7fffffffLL) return fe_fail(FE_EINVAL, "cell operator: grid too large");
-  k_cell_apply<P><<<(unsigned)grid, S::NTHR, 0, m->stream>>>(cf, x, ycell, m->nx, m->ny, m->NX,
-                                                             m->NY);
+  if (m->ny > 65535 || m->nz > 65535) return fe_fail(FE_EINVAL, "cell operator: mesh too large");
+  k_cell_apply<P><<<dim3(nstrip, m->ny, m->nz), S::NTHR, 0, m->stream>>>(cf, x, ycell, m->nx,
+                                                                         m->ny, m->NX, m->NY);
   fe_count_launch();
-  const int64_t nb = (m->n_phi + 255) / 256;
-  k_cell_gather<<<(unsigned)nb, 256, 0, m->stream>>>(ycell, y, m->p, m->nx, m->ny, m->nz, m->NX,
-                                                     m->NY, m->n_phi);
+  const int planes = m->NZ < 65535 ? m->NZ : 65535;
+  k_cell_gather<P><<<dim3((m->NX + 31) / 32, (m->NY + 7) / 8, planes), dim3(32, 8), 0, m->stream>>>(
+      ycell, y, m->nx, m->ny, m->nz, m->NX, m->NY);
   fe_count_launch();
   FE_CUDA(cudaGetLastError());
   return FE_OK;

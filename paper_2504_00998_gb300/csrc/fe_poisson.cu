@@ -108,37 +108,55 @@ __global__ void k_setup(PGeom g, fe_poisson_bc bc, const double* __restrict__ ma
   }
 }
 
+// Block sums in a fixed order (so every reduction is reproducible): a shuffle tree inside
+// each warp, then every warp reduces the per-warp sums the same way.  blockDim.x is a multiple
+// of 32 (at most 1024); every thread receives the total; one barrier per call (two with the
+// barrier that lets a later call reuse the staging array).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+  t = __shfl_sync(0xffffffffu, warp_sum(t), 0);
+  __syncthreads();
+  return t;
+}
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double wa[32], wb[32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) { wa[threadIdx.x >> 5] = a; wb[threadIdx.x >> 5] = b; }
+  __syncthreads();
+  const bool in = lane < (int)(blockDim.x >> 5);
+  a = __shfl_sync(0xffffffffu, warp_sum(in ? wa[lane] : 0.0), 0);
+  b = __shfl_sync(0xffffffffu, warp_sum(in ? wb[lane] : 0.0), 0);
+  __syncthreads();
+}
+
 // partial sums of x (y == nullptr) or x.y, accumulated in double; one partial per block
 template <typename V>
 __global__ void k_psum(const V* __restrict__ x, const V* __restrict__ y, int64_t n,
                        double* __restrict__ part) {
-  __shared__ double sh[fe::RED_THREADS];
   V s = V(0);   // a thread's few terms in the vector precision, the block sum in double
   for (int64_t i = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x; i < n;
        i += (int64_t)fe::RED_BLOCKS * fe::RED_THREADS)
     s += y ? x[i] * y[i] : x[i];
-  sh[threadIdx.x] = (double)s;
-  __syncthreads();
-  for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  const double t = block_sum((double)s);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 __device__ double block_sum_partials(const double* part) {
-  __shared__ double sh[fe::RED_BLOCKS];
   double s = 0.0;
   for (int i = threadIdx.x; i < fe::RED_BLOCKS; i += blockDim.x) s += part[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  double r = sh[0];
-  __syncthreads();
-  return r;
+  return block_sum(s);
 }
 
 // CEF load projection: f <- f - (sum f / sum M) M
@@ -179,7 +197,6 @@ __global__ void k_precond(V* __restrict__ r, V* __restrict__ z, const V* __restr
                           int64_t n, double* __restrict__ part_rz, double* __restrict__ part_rr,
                           const double* __restrict__ cy, int64_t plane,
                           const double* __restrict__ mean_part) {
-  __shared__ double sh1[fe::RED_THREADS], sh2[fe::RED_THREADS];
   double mean_d = 0.0;
   if (project) mean_d = mean_part ? block_sum_partials(mean_part) * (1.0 / (double)n) : s->mean;
   const V mean = (V)mean_d;
@@ -194,14 +211,9 @@ __global__ void k_precond(V* __restrict__ r, V* __restrict__ z, const V* __restr
     a1 += ri * zi;
     a2 += ri * ri;
   }
-  sh1[threadIdx.x] = (double)a1;
-  sh2[threadIdx.x] = (double)a2;
-  __syncthreads();
-  for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) { sh1[threadIdx.x] += sh1[threadIdx.x + w]; sh2[threadIdx.x] += sh2[threadIdx.x + w]; }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) { part_rz[blockIdx.x] = sh1[0]; part_rr[blockIdx.x] = sh2[0]; }
+  double t1 = (double)a1, t2 = (double)a2;
+  block_sum2(t1, t2);
+  if (threadIdx.x == 0) { part_rz[blockIdx.x] = t1; part_rr[blockIdx.x] = t2; }
 }
 
 // first iteration: p = z, rz, rr, |b|^2
@@ -244,7 +256,6 @@ __global__ void k_update_xr(V* __restrict__ x, V* __restrict__ r, const V* __res
                             const V* __restrict__ q, const unsigned char* __restrict__ mask,
                             CgState* s, int64_t n, double* __restrict__ part,
                             const double* __restrict__ pq_part) {
-  __shared__ double sh[fe::RED_THREADS];
   const double pq = block_sum_partials(pq_part);
   const double al = (s->done || pq == 0.0) ? 0.0 : s->rz / pq;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -263,13 +274,8 @@ __global__ void k_update_xr(V* __restrict__ x, V* __restrict__ r, const V* __res
     }
     acc += ri;
   }
-  sh[threadIdx.x] = (double)acc;
-  __syncthreads();
-  for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  const double t = block_sum((double)acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // beta = rz_new / rz; convergence test on |r|^2; iteration count
@@ -366,24 +372,198 @@ __global__ void k_vbare(PGeom g, const double* __restrict__ phi, const double* _
 // sums over free nodes; the coarse matrix Ac = R K R^T couples planes that share a cell layer.
 
 // out[gz] = sum of x over the free nodes of plane gz (x == nullptr: the free-node count);
+// ---- float vectors, four nodes per access --------------------------------------------------
+// Used when a z plane holds a multiple of four nodes (a group of four never straddles a plane)
+// and the arrays are 16-byte (vectors) and 4-byte (mask) aligned.  A thread issues the loads of
+// up to V4B groups before using any of them, so that one round trip to L2 covers its share;
+// the sums keep the scalar kernels' structure (a thread's terms in float, the block sum in
+// double, one partial per block).
+constexpr int V4B = 4;
+constexpr int64_t V4S = (int64_t)fe::RED_BLOCKS * fe::RED_THREADS;
+
+__device__ __forceinline__ void block_partial(float v, double* __restrict__ part) {
+  const double t = block_sum((double)v);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__device__ __forceinline__ float sum4(const float4& a) { return a.x + a.y + a.z + a.w; }
+
+// partial sums of x (y == nullptr) or x.y over n4 groups
+__global__ void k_psum4(const float* __restrict__ x, const float* __restrict__ y, int64_t n4,
+                        double* __restrict__ part) {
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const float4* y4 = reinterpret_cast<const float4*>(y);
+  const int64_t g = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x;
+  float s = 0.f;
+  for (int64_t q0 = g; q0 < n4; q0 += V4B * V4S) {
+    float4 a[V4B], b[V4B];
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t q = q0 + u * V4S;
+      if (q < n4) {
+        a[u] = x4[q];
+        if (y) b[u] = y4[q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      if (q0 + u * V4S >= n4) continue;
+      s += y ? a[u].x * b[u].x + a[u].y * b[u].y + a[u].z * b[u].z + a[u].w * b[u].w : sum4(a[u]);
+    }
+  }
+  block_partial(s, part);
+}
+
+// alpha from the p.q partials (every block; block 0 records it); x += alpha p, r -= alpha q
+// on free nodes; partials of sum r
+__global__ void k_update_xr4(float* __restrict__ x, float* __restrict__ r,
+                             const float* __restrict__ p, const float* __restrict__ q,
+                             const unsigned char* __restrict__ mask, CgState* s, int64_t n4,
+                             double* __restrict__ part, const double* __restrict__ pq_part) {
+  const double pq = block_sum_partials(pq_part);
+  const double al = (s->done || pq == 0.0) ? 0.0 : s->rz / pq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    s->pq = pq;
+    s->alpha = al;
+  }
+  const float a = (float)al;
+  float4* x4 = reinterpret_cast<float4*>(x);
+  float4* r4 = reinterpret_cast<float4*>(r);
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  const uchar4* m4 = reinterpret_cast<const uchar4*>(mask);
+  const int64_t g = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x;
+  float acc = 0.f;
+  for (int64_t q0 = g; q0 < n4; q0 += V4B * V4S) {
+    float4 xv[V4B], rv[V4B], pv[V4B], qv[V4B];
+    uchar4 mv[V4B];
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t k = q0 + u * V4S;
+      if (k < n4) { xv[u] = x4[k]; rv[u] = r4[k]; pv[u] = p4[k]; qv[u] = q4[k]; mv[u] = m4[k]; }
+    }
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t k = q0 + u * V4S;
+      if (k >= n4) continue;
+      if (!mv[u].x) { xv[u].x += a * pv[u].x; rv[u].x -= a * qv[u].x; }
+      if (!mv[u].y) { xv[u].y += a * pv[u].y; rv[u].y -= a * qv[u].y; }
+      if (!mv[u].z) { xv[u].z += a * pv[u].z; rv[u].z -= a * qv[u].z; }
+      if (!mv[u].w) { xv[u].w += a * pv[u].w; rv[u].w -= a * qv[u].w; }
+      x4[k] = xv[u];
+      r4[k] = rv[u];
+      acc += sum4(rv[u]);
+    }
+  }
+  block_partial(acc, part);
+}
+
+// r -= mean (CEF); z = Dinv r + coarse correction of the node's plane on free nodes; partials
+// of r.z and r.r (mean_part: the partials of sum r, or nullptr for the mean in the state)
+__global__ void k_precond4(float* __restrict__ r, float* __restrict__ z,
+                           const float* __restrict__ dinv, const unsigned char* __restrict__ mask,
+                           const CgState* s, int project, int64_t n4, double* __restrict__ part_rz,
+                           double* __restrict__ part_rr, const double* __restrict__ cy,
+                           uint32_t plane4, const double* __restrict__ mean_part, int64_t n) {
+  double mean_d = 0.0;
+  if (project) mean_d = mean_part ? block_sum_partials(mean_part) * (1.0 / (double)n) : s->mean;
+  const float mean = (float)mean_d;
+  float4* r4 = reinterpret_cast<float4*>(r);
+  float4* z4 = reinterpret_cast<float4*>(z);
+  const float4* d4 = reinterpret_cast<const float4*>(dinv);
+  const uchar4* m4 = reinterpret_cast<const uchar4*>(mask);
+  const int64_t g = blockIdx.x * (int64_t)fe::RED_THREADS + threadIdx.x;
+  float a1 = 0.f, a2 = 0.f;
+  for (int64_t q0 = g; q0 < n4; q0 += V4B * V4S) {
+    float4 rv[V4B], dv[V4B];
+    uchar4 mv[V4B];
+    float cv[V4B];
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t k = q0 + u * V4S;
+      if (k < n4) {
+        rv[u] = r4[k];
+        dv[u] = d4[k];
+        mv[u] = m4[k];
+        cv[u] = cy ? (float)cy[(uint32_t)k / plane4] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t k = q0 + u * V4S;
+      if (k >= n4) continue;
+      float4 ri = rv[u], zi;
+      if (project) {
+        ri.x -= mean; ri.y -= mean; ri.z -= mean; ri.w -= mean;
+        r4[k] = ri;
+      }
+      zi.x = mv[u].x ? 0.f : dv[u].x * ri.x + cv[u];
+      zi.y = mv[u].y ? 0.f : dv[u].y * ri.y + cv[u];
+      zi.z = mv[u].z ? 0.f : dv[u].z * ri.z + cv[u];
+      zi.w = mv[u].w ? 0.f : dv[u].w * ri.w + cv[u];
+      z4[k] = zi;
+      a1 += ri.x * zi.x + ri.y * zi.y + ri.z * zi.z + ri.w * zi.w;
+      a2 += ri.x * ri.x + ri.y * ri.y + ri.z * ri.z + ri.w * ri.w;
+    }
+  }
+  double t1 = (double)a1, t2 = (double)a2;
+  block_sum2(t1, t2);
+  if (threadIdx.x == 0) { part_rz[blockIdx.x] = t1; part_rr[blockIdx.x] = t2; }
+}
+
+// p = z + beta p (skipped once converged)
+__global__ void k_update_p4(float* __restrict__ p, const float* __restrict__ z, const CgState* s,
+                            int64_t n4) {
+  if (s->done && s->alpha == 0.0) return;
+  const float b = (float)s->beta;
+  float4* p4 = reinterpret_cast<float4*>(p);
+  const float4* z4 = reinterpret_cast<const float4*>(z);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n4;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const float4 zv = z4[k];
+    float4 pv = p4[k];
+    pv.x = zv.x + b * pv.x; pv.y = zv.y + b * pv.y; pv.z = zv.z + b * pv.z; pv.w = zv.w + b * pv.w;
+    p4[k] = pv;
+  }
+}
+
+// sum of x over the free nodes of plane blockIdx.x (plane4 groups per plane)
+__global__ void k_plane_sum4(const float* __restrict__ x, const unsigned char* __restrict__ mask,
+                             int64_t plane4, double* __restrict__ out) {
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  const uchar4* m4 = reinterpret_cast<const uchar4*>(mask);
+  const int64_t base = (int64_t)blockIdx.x * plane4;
+  float a = 0.f;
+  for (int64_t i0 = threadIdx.x; i0 < plane4; i0 += V4B * fe::RED_THREADS) {
+    float4 xv[V4B];
+    uchar4 mv[V4B];
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t i = i0 + u * fe::RED_THREADS;
+      if (i < plane4) { xv[u] = x4[base + i]; mv[u] = m4[base + i]; }
+    }
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      if (i0 + u * fe::RED_THREADS >= plane4) continue;
+      a += (mv[u].x ? 0.f : xv[u].x) + (mv[u].y ? 0.f : xv[u].y) + (mv[u].z ? 0.f : xv[u].z) +
+           (mv[u].w ? 0.f : xv[u].w);
+    }
+  }
+  block_partial(a, out);
+}
+
 // one block of RED_THREADS per plane, deterministic order
 template <typename V>
 __global__ void k_plane_sum(const V* __restrict__ x, const unsigned char* __restrict__ mask,
                             int64_t plane, double* __restrict__ out) {
-  __shared__ double sh[fe::RED_THREADS];
   const int64_t base = (int64_t)blockIdx.x * plane;
   V a = V(0);
   for (int64_t i = threadIdx.x; i < plane; i += fe::RED_THREADS) {
     const int64_t id = base + i;
     if (!mask[id]) a += x ? x[id] : V(1);
   }
-  sh[threadIdx.x] = (double)a;
-  __syncthreads();
-  for (int w = fe::RED_THREADS / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+  const double t = block_sum((double)a);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
 }
 
 // v = sum of the coarse basis functions of the planes gz = color (mod period)
@@ -697,39 +877,95 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
   const int gb = fe::grid_for(n);
   const int cblocks = (nzp + COARSE_COLS - 1) / COARSE_COLS;
   const size_t csmem = sizeof(double) * ((size_t)nzp + 4 * COARSE_COLS);
+  const double* cy = b.Ainv ? b.cy : nullptr;
+  // four nodes per access for float vectors whose planes hold a multiple of four nodes
+  auto al16 = [](const void* q) { return ((uintptr_t)q % 16) == 0; };
+  bool v4 = false;
+  if constexpr (std::is_same<V, float>::value)
+    v4 = plane % 4 == 0 && al16(b.x) && al16(b.r) && al16(b.z) && al16(b.p) && al16(b.q) &&
+         al16(b.dinv) && ((uintptr_t)b.mask % 4) == 0;
+  const int64_t n4 = n / 4;
+  auto psum = [&](const V* x, const V* y, double* part) {
+    if constexpr (std::is_same<V, float>::value) {
+      if (v4) {
+        k_psum4<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(x, y, n4, part); fe_count_launch();
+        return;
+      }
+    }
+    k_psum<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(x, y, n, part); fe_count_launch();
+  };
+  auto precond = [&](const double* mean_part) {
+    if constexpr (std::is_same<V, float>::value) {
+      if (v4) {
+        k_precond4<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s,
+                                                               project, n4, b.pc, b.pd, cy,
+                                                               (uint32_t)(plane / 4), mean_part, n);
+        fe_count_launch();
+        return;
+      }
+    }
+    k_precond<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project,
+                                                             n, b.pc, b.pd, cy, plane, mean_part);
+    fe_count_launch();
+  };
   auto coarse = [&](const double* mean_part) {
     if (!b.Ainv) return;
-    k_plane_sum<V><<<nzp, fe::RED_THREADS, 0, st>>>(b.r, b.mask, plane, b.csum); fe_count_launch();
+    bool done4 = false;
+    if constexpr (std::is_same<V, float>::value) {
+      if (v4) {
+        k_plane_sum4<<<nzp, fe::RED_THREADS, 0, st>>>(b.r, b.mask, plane / 4, b.csum);
+        fe_count_launch();
+        done4 = true;
+      }
+    }
+    if (!done4) {
+      k_plane_sum<V><<<nzp, fe::RED_THREADS, 0, st>>>(b.r, b.mask, plane, b.csum); fe_count_launch();
+    }
     k_coarse_apply<<<cblocks, 4 * COARSE_COLS, csmem, st>>>(b.csum, b.ccnt, b.Ainv, b.s, project,
                                                             nzp, b.cy, mean_part, 1.0 / (double)n);
     fe_count_launch();
   };
-  const double* cy = b.Ainv ? b.cy : nullptr;
   CgState s0 = {};
   s0.maxit = maxit;
   FE_CUDA(cudaMemcpyAsync(b.s, &s0, sizeof(CgState), cudaMemcpyHostToDevice, st));
   if (project) {
-    k_psum<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, nullptr, n, b.pa); fe_count_launch();
+    psum(b.r, nullptr, b.pa);
     k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(b.pa, b.s, 1.0 / (double)n); fe_count_launch();
   }
   coarse(nullptr);
-  k_precond<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project, n,
-                                                           b.pc, b.pd, cy, plane, nullptr); fe_count_launch();
+  precond(nullptr);
   k_fin_init<<<1, fe::RED_BLOCKS, 0, st>>>(b.pc, b.pd, b.s, rtol, tol2_abs); fe_count_launch();
   k_copy<V><<<gb, 256, 0, st>>>(b.z, b.p, n); fe_count_launch();
   FE_CUDA(cudaGetLastError());
 
   auto iteration = [&]() -> fe_status {
     FE_TRY(apply_K_v(m, b.p, b.q));
-    k_psum<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.p, b.q, n, b.pa); fe_count_launch();
-    k_update_xr<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.x, b.r, b.p, b.q, b.mask, b.s, n,
-                                                               b.pb, b.pa); fe_count_launch();
+    psum(b.p, b.q, b.pa);
+    bool xr4 = false;
+    if constexpr (std::is_same<V, float>::value) {
+      if (v4) {
+        k_update_xr4<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.x, b.r, b.p, b.q, b.mask, b.s, n4,
+                                                                 b.pb, b.pa);
+        fe_count_launch();
+        xr4 = true;
+      }
+    }
+    if (!xr4) {
+      k_update_xr<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.x, b.r, b.p, b.q, b.mask, b.s, n,
+                                                                 b.pb, b.pa);
+      fe_count_launch();
+    }
     coarse(b.pb);
-    k_precond<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project,
-                                                             n, b.pc, b.pd, cy, plane, b.pb);
-    fe_count_launch();
+    precond(b.pb);
     k_fin_beta<<<1, fe::RED_BLOCKS, 0, st>>>(b.pc, b.pd, b.s); fe_count_launch();
-    k_update_p<V><<<gb, 256, 0, st>>>(b.p, b.z, b.s, n); fe_count_launch();
+    bool p4 = false;
+    if constexpr (std::is_same<V, float>::value) {
+      if (v4) {
+        k_update_p4<<<fe::grid_for(n4), 256, 0, st>>>(b.p, b.z, b.s, n4); fe_count_launch();
+        p4 = true;
+      }
+    }
+    if (!p4) { k_update_p<V><<<gb, 256, 0, st>>>(b.p, b.z, b.s, n); fe_count_launch(); }
     return FE_OK;
   };
   const int per_graph = 16;
@@ -758,13 +994,11 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
   }
   auto replaced = [&](bool restart) {
     if (project) {
-      k_psum<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, nullptr, n, b.pa); fe_count_launch();
+      psum(b.r, nullptr, b.pa);
       k_fin_mean<<<1, fe::RED_BLOCKS, 0, st>>>(b.pa, b.s, 1.0 / (double)n); fe_count_launch();
     }
     coarse(nullptr);
-    k_precond<V><<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project,
-                                                             n, b.pc, b.pd, cy, plane, nullptr);
-    fe_count_launch();
+    precond(nullptr);
     k_fin_replace<<<1, fe::RED_BLOCKS, 0, st>>>(b.pc, b.pd, b.s); fe_count_launch();
     if (restart) { k_copy<V><<<gb, 256, 0, st>>>(b.z, b.p, n); fe_count_launch(); }
   };
