@@ -31,6 +31,7 @@ constexpr double FOUR_PI = 12.566370614359172;
 struct CgState {
   double rz, rz_new, pq, rr, alpha, beta, bnorm2, tol2, mean;
   int done, iters, maxit;
+  unsigned int ticket[2];   // finished-block counters of the single-pass reductions (0 at rest)
 };
 
 struct PGeom {
@@ -552,6 +553,207 @@ __global__ void k_plane_sum4(const float* __restrict__ x, const unsigned char* _
   block_partial(a, out);
 }
 
+// ---- float iteration with the plane coarse space: seven launches per iteration ----------------
+// The grid-wide scalars (alpha, the mean, beta and the convergence test) are finished by the
+// last block of the kernel that produces their partials (a ticket taken after each block's
+// partial is visible), so no single-block finishing launch sits between the vector kernels.
+// The last block sums the partials in index order, as a separate finishing kernel would.
+
+// returns true in every thread of the block that finished last (ticket reset for the next use)
+__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+__device__ __forceinline__ double sum_partials_cg(const double* part, int np) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += __ldcg(part + i);
+  return block_sum(s);
+}
+
+// p.q partials; the last block sets pq and alpha = r.z / p.q
+__global__ void k_psum4_alpha(const float* __restrict__ p, const float* __restrict__ q, int64_t n4,
+                              double* __restrict__ part, CgState* s) {
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float acc = 0.f;
+  for (int64_t q0 = g; q0 < n4; q0 += V4B * stride) {
+    float4 a[V4B], b[V4B];
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t k = q0 + u * stride;
+      if (k < n4) { a[u] = p4[k]; b[u] = q4[k]; }
+    }
+#pragma unroll
+    for (int u = 0; u < V4B; ++u)
+      if (q0 + u * stride < n4)
+        acc += a[u].x * b[u].x + a[u].y * b[u].y + a[u].z * b[u].z + a[u].w * b[u].w;
+  }
+  const double t = block_sum((double)acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (last_block(&s->ticket[0])) {
+    const double pq = sum_partials_cg(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      s->pq = pq;
+      s->alpha = (s->done || pq == 0.0) ? 0.0 : s->rz / pq;
+      s->ticket[0] = 0;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q on free nodes, by plane segments: block b takes segment b % nseg of
+// plane b / nseg (seglen groups of four nodes) and writes the segment's sum of r to seg[b]
+__global__ void k_update_xr4s(float* __restrict__ x, float* __restrict__ r,
+                              const float* __restrict__ p, const float* __restrict__ q,
+                              const unsigned char* __restrict__ mask, const CgState* s,
+                              int64_t plane4, int nseg, int seglen, double* __restrict__ seg) {
+  const float a = (float)s->alpha;
+  const int pl = blockIdx.x / nseg, sg = blockIdx.x - pl * nseg;
+  const int64_t lo = (int64_t)pl * plane4 + (int64_t)sg * seglen;
+  const int64_t hi = min((int64_t)pl * plane4 + plane4, lo + seglen);
+  float4* x4 = reinterpret_cast<float4*>(x);
+  float4* r4 = reinterpret_cast<float4*>(r);
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  const uchar4* m4 = reinterpret_cast<const uchar4*>(mask);
+  float acc = 0.f;
+  for (int64_t k0 = lo + threadIdx.x; k0 < hi; k0 += V4B * (int64_t)blockDim.x) {
+    float4 xv[V4B], rv[V4B], pv[V4B], qv[V4B];
+    uchar4 mv[V4B];
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t k = k0 + u * (int64_t)blockDim.x;
+      if (k < hi) { xv[u] = x4[k]; rv[u] = r4[k]; pv[u] = p4[k]; qv[u] = q4[k]; mv[u] = m4[k]; }
+    }
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t k = k0 + u * (int64_t)blockDim.x;
+      if (k >= hi) continue;
+      if (!mv[u].x) { xv[u].x += a * pv[u].x; rv[u].x -= a * qv[u].x; }
+      if (!mv[u].y) { xv[u].y += a * pv[u].y; rv[u].y -= a * qv[u].y; }
+      if (!mv[u].z) { xv[u].z += a * pv[u].z; rv[u].z -= a * qv[u].z; }
+      if (!mv[u].w) { xv[u].w += a * pv[u].w; rv[u].w -= a * qv[u].w; }
+      x4[k] = xv[u];
+      r4[k] = rv[u];
+      acc += sum4(rv[u]);
+    }
+  }
+  const double t = block_sum((double)acc);
+  if (threadIdx.x == 0) seg[blockIdx.x] = t;
+}
+
+// The coarse correction from the plane-segment sums: b_k = (sum of plane k's segments) -
+// mean cnt_k, mean = (sum of all segments) / n under the CEF projection (block 0 records it),
+// then one warp per coarse unknown j: y_j = sum_k Ainv[j][k] b_k (Ainv symmetric), in float.
+__global__ void k_coarse_apply4(const double* __restrict__ seg, int nseg,
+                                const double* __restrict__ cnt, const double* __restrict__ Ainv,
+                                CgState* st, int project, int nz, double inv_n,
+                                float* __restrict__ yf) {
+  extern __shared__ double cb[];   // b[nz]
+  double loc = 0.0;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    double sk = 0.0;
+    for (int t = 0; t < nseg; ++t) sk += seg[(int64_t)k * nseg + t];
+    cb[k] = sk;
+    loc += sk;
+  }
+  const double total = block_sum(loc);
+  const double mean = project ? total * inv_n : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->mean = mean;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) cb[k] -= mean * cnt[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j < nz) {
+    const double* row = Ainv + (int64_t)j * nz;
+    double a = 0.0;
+    for (int k = lane; k < nz; k += 32) a += row[k] * cb[k];
+    a = warp_sum(a);
+    if (lane == 0) yf[j] = (float)a;
+  }
+}
+
+// r -= mean (the state's, CEF); z = Dinv r + yf[plane] on free nodes; r.z and r.r partials; the
+// last block finishes beta, r.z, |r|^2, the iteration count and the convergence test
+__global__ void k_precond4_beta(float* __restrict__ r, float* __restrict__ z,
+                                const float* __restrict__ dinv,
+                                const unsigned char* __restrict__ mask, CgState* s, int project,
+                                int64_t n4, double* __restrict__ part_rz,
+                                double* __restrict__ part_rr, const float* __restrict__ yf,
+                                uint32_t plane4) {
+  const float mean = project ? (float)s->mean : 0.f;
+  float4* r4 = reinterpret_cast<float4*>(r);
+  float4* z4 = reinterpret_cast<float4*>(z);
+  const float4* d4 = reinterpret_cast<const float4*>(dinv);
+  const uchar4* m4 = reinterpret_cast<const uchar4*>(mask);
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float a1 = 0.f, a2 = 0.f;
+  for (int64_t q0 = g; q0 < n4; q0 += V4B * stride) {
+    float4 rv[V4B], dv[V4B];
+    uchar4 mv[V4B];
+    float cv[V4B];
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t k = q0 + u * stride;
+      if (k < n4) {
+        rv[u] = r4[k];
+        dv[u] = d4[k];
+        mv[u] = m4[k];
+        cv[u] = yf[(uint32_t)k / plane4];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < V4B; ++u) {
+      const int64_t k = q0 + u * stride;
+      if (k >= n4) continue;
+      float4 ri = rv[u], zi;
+      if (project) {
+        ri.x -= mean; ri.y -= mean; ri.z -= mean; ri.w -= mean;
+        r4[k] = ri;
+      }
+      zi.x = mv[u].x ? 0.f : dv[u].x * ri.x + cv[u];
+      zi.y = mv[u].y ? 0.f : dv[u].y * ri.y + cv[u];
+      zi.z = mv[u].z ? 0.f : dv[u].z * ri.z + cv[u];
+      zi.w = mv[u].w ? 0.f : dv[u].w * ri.w + cv[u];
+      z4[k] = zi;
+      a1 += ri.x * zi.x + ri.y * zi.y + ri.z * zi.z + ri.w * zi.w;
+      a2 += ri.x * ri.x + ri.y * ri.y + ri.z * ri.z + ri.w * ri.w;
+    }
+  }
+  double t1 = (double)a1, t2 = (double)a2;
+  block_sum2(t1, t2);
+  if (threadIdx.x == 0) { part_rz[blockIdx.x] = t1; part_rr[blockIdx.x] = t2; }
+  if (last_block(&s->ticket[1])) {
+    double rz = 0.0, rr = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+      rz += __ldcg(part_rz + i);
+      rr += __ldcg(part_rr + i);
+    }
+    block_sum2(rz, rr);
+    if (threadIdx.x == 0) {
+      if (!s->done) {
+        s->beta = s->rz == 0.0 ? 0.0 : rz / s->rz;
+        s->rz = rz;
+        s->rr = rr;
+        s->iters += 1;
+        if (rr <= s->tol2 || s->iters >= s->maxit) s->done = 1;
+      } else {
+        s->beta = 0.0;
+      }
+      s->ticket[1] = 0;
+    }
+  }
+}
+
 // one block of RED_THREADS per plane, deterministic order
 template <typename V>
 __global__ void k_plane_sum(const V* __restrict__ x, const unsigned char* __restrict__ mask,
@@ -845,6 +1047,9 @@ struct CgBuf {
   const double* ccnt;
   double* csum;
   double* cy;
+  double* seg;                 // plane-segment sums of r (float path with the coarse space)
+  float* cyf;                  // float coarse correction per plane
+  int nseg;                    // segments per plane
 };
 
 fe_status apply_K_v(fe_mesh* m, const double* x, double* y) { return fe_poisson_apply_K(m, x, y); }
@@ -938,8 +1143,28 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
   k_copy<V><<<gb, 256, 0, st>>>(b.z, b.p, n); fe_count_launch();
   FE_CUDA(cudaGetLastError());
 
+  // float, four nodes per access, coarse space present: the seven-launch iteration
+  const bool fused = v4 && b.Ainv && b.nseg > 0 && b.seg && b.cyf;
+  const int seglen = fused ? (int)((plane / 4 + b.nseg - 1) / b.nseg) : 0;
   auto iteration = [&]() -> fe_status {
     FE_TRY(apply_K_v(m, b.p, b.q));
+    if constexpr (std::is_same<V, float>::value) {
+      if (fused) {
+        k_psum4_alpha<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.p, b.q, n4, b.pa, b.s);
+        fe_count_launch();
+        k_update_xr4s<<<nzp * b.nseg, 256, 0, st>>>(b.x, b.r, b.p, b.q, b.mask, b.s, plane / 4,
+                                                    b.nseg, seglen, b.seg);
+        fe_count_launch();
+        k_coarse_apply4<<<(nzp + 7) / 8, 256, sizeof(double) * nzp, st>>>(
+            b.seg, b.nseg, b.ccnt, b.Ainv, b.s, project, nzp, 1.0 / (double)n, b.cyf);
+        fe_count_launch();
+        k_precond4_beta<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(
+            b.r, b.z, b.dinv, b.mask, b.s, project, n4, b.pc, b.pd, b.cyf, (uint32_t)(plane / 4));
+        fe_count_launch();
+        k_update_p4<<<fe::grid_for(n4), 256, 0, st>>>(b.p, b.z, b.s, n4); fe_count_launch();
+        return FE_OK;
+      }
+    }
     psum(b.p, b.q, b.pa);
     bool xr4 = false;
     if constexpr (std::is_same<V, float>::value) {
@@ -1055,8 +1280,13 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   // partials, coarse correction, two states, mask
   void* wsp;
   const size_t nd = (size_t)n * 6, nf = mixed ? (size_t)n * 6 : 0;
+  // float path, planes of a multiple of four nodes: plane segments of at most 1024 groups of
+  // four nodes (one batch of loads per thread in the segment kernel)
+  const int64_t plane_n = (int64_t)m->NX * m->NY;
+  const int nseg = (mixed && plane_n % 4 == 0) ? (int)((plane_n / 4 + 1023) / 1024) : 0;
   size_t bytes = nd * sizeof(double) + nf * sizeof(float) + 64 +
-                 (4 * fe::RED_BLOCKS + (size_t)nzp) * sizeof(double) + 2 * sizeof(CgState) + n + 256;
+                 (4 * fe::RED_BLOCKS + (size_t)nzp) * sizeof(double) + 2 * sizeof(CgState) + n + 256 +
+                 (size_t)nzp * nseg * sizeof(double) + (size_t)nzp * sizeof(float) + 256;
   FE_TRY(fe_ws(m, WS_CG, bytes, &wsp));
   double* f = (double*)wsp;
   double* dinv = f + n;
@@ -1073,6 +1303,8 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   CgState* s = (CgState*)(cyv + nzp);
   CgState* sref = s + 1;
   unsigned char* mask = (unsigned char*)(sref + 1);
+  double* segp = (double*)(((uintptr_t)(mask + n) + 255) & ~(uintptr_t)255);
+  float* cyf = (float*)(segp + (size_t)nzp * nseg);
   const int project = bc->kind == FE_BIAS_CEF;
   const double* rh = rho ? rho : m->d_rho;
   const int gb = fe::grid_for(n);
@@ -1137,7 +1369,8 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
     k_to_float<<<gb, 256, 0, st>>>(dinv, dinvf, n); fe_count_launch();
     k_to_float<<<gb, 256, 0, st>>>(r, rf, n); fe_count_launch();
     FE_CUDA(cudaMemsetAsync(df, 0, sizeof(float) * n, st));
-    CgBuf<float> bf{df, rf, zf, pf, qf, dinvf, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv};
+    CgBuf<float> bf{df, rf, zf, pf, qf, dinvf, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv,
+                    segp, cyf, nseg};
     double rr_last = rr;
     int it_last = 0, stalls = 0, breakdowns = 0;
     auto reliable = [&](const CgState& cs, int* action) -> fe_status {
@@ -1177,7 +1410,8 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   }
   if (rr > tol2 && used < bc->max_iter) {
     // double CG from the current phi (the whole solve when the mixed mode is off)
-    CgBuf<double> bd{phi, r, z, p, q, dinv, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv};
+    CgBuf<double> bd{phi, r, z, p, q, dinv, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv,
+                     nullptr, nullptr, 0};
     FE_TRY(cg_run<double>(m, bd, project, bc->rtol, tol2, bc->max_iter - used, use_graph,
                           &gexec_d.e, &gk_d, &hs, no_hook));
     used += hs.iters;
