@@ -87,6 +87,7 @@ struct KronCoef {
   double wz[FE_MAXN1];    // GLL weights (for the z mass factor of a plane)
   double zin;             // J^-1/2 (or 1 for the Poisson operator)
   double zout;            // 1/2 J^-1/2 (or 1)
+  double ax, ay;          // the in-plane stiffness scales hy hz / (2 hx), hx hz / (2 hy)
   int mass_scale;         // 1: Hamiltonian (mass-scaled), 0: plain K
 };
 

@@ -30,6 +30,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "fe_gll_tables.h"
 #include "fe_internal.h"
 
 namespace fe {
@@ -55,6 +56,7 @@ struct KronCoefT {
   T rsq[FE_MAXN1], sq[FE_MAXN1];
   T rsq_face, sq_face, face_fix;
   T zout, izout;
+  T ax, ay;   // in-plane stiffness scales (used with the compile-time shape tables)
   int mass_scale;
 };
 
@@ -89,6 +91,8 @@ inline KronCoefT<T> convert_coef(const KronCoef& c) {
   o.face_fix = c.mass_scale ? (T)std::sqrt(2.0) : T(1);
   o.zout = (T)c.zout;
   o.izout = (T)(1.0 / c.zout);
+  o.ax = (T)c.ax;
+  o.ay = (T)c.ay;
   o.mass_scale = c.mass_scale;
   return o;
 }
@@ -189,8 +193,11 @@ struct KronTileT {
 
 // One CTA's work: xy block bxy (x fastest), vector tile vti, z segment zsi.
 // FULL: every xy block is complete and every vector tile full, so no ownership, edge or
-// ragged-vector test is needed anywhere in the sweep
-template <typename T, int CH, class TL, bool FULL>
+// ragged-vector test is needed anywhere in the sweep.
+// CT (float Hamiltonian): the in-plane contractions take the shape-only tables M1 sig and
+// K1 sig as compile-time constants (FFMA immediates instead of constant-bank loads) and apply
+// the mesh scales ay, ax as one multiply per y output and one FMA per x output.
+template <typename T, int CH, class TL, bool FULL, bool CT>
 __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom& g,
                                           const KronIO<T>& io, int bxy, int vti, int zsi) {
   using C = Chunk<T, CH>;
@@ -397,6 +404,20 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
     }
   };
 
+  // in-plane 1D coefficients: the mesh's tables, or (CT) the compile-time shape tables
+  auto cYM = [&](int j, int k) -> T {
+    if constexpr (CT) return (T)gll_ms<P>(j, k); else return cf.AyM[j][k];
+  };
+  auto cYK = [&](int j, int k) -> T {
+    if constexpr (CT) return (T)gll_ks<P>(j, k); else return cf.AyK[j][k];
+  };
+  auto cXM = [&](int j, int k) -> T {
+    if constexpr (CT) return (T)gll_ms<P>(j, k); else return cf.AxM[j][k];
+  };
+  auto cXK = [&](int j, int k) -> T {
+    if constexpr (CT) return (T)gll_ks<P>(j, k); else return cf.AxK[j][k];
+  };
+
   // scalar-lane items of the in-plane phases (used when each thread has at most one)
   constexpr int NL = NCH * CH;
   int y_ibase = 0, y_obase = 0, x_ibase = 0, x_obase = 0;
@@ -449,23 +470,26 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
           b.zero();
 #pragma unroll
           for (int kk = 0; kk <= P; ++kk) {
-            a.fma(cf.AyM[j][kk], own[kk]);
-            b.fma(cf.AyK[j][kk], own[kk]);
+            a.fma(cYM(j, kk), own[kk]);
+            b.fma(cYK(j, kk), own[kk]);
           }
           if (j == 0) {
 #pragma unroll
             for (int kk = 0; kk < P; ++kk) {
-              a.fma(cf.AyM[P][kk], prv[kk]);
-              b.fma(cf.AyK[P][kk], prv[kk]);
+              a.fma(cYM(P, kk), prv[kk]);
+              b.fma(cYK(P, kk), prv[kk]);
             }
-            a.fma(cf.AyM[P][P], own[0]);
-            b.fma(cf.AyK[P][P], own[0]);
+            a.fma(cYM(P, P), own[0]);
+            b.fma(cYK(P, P), own[0]);
           }
+          if constexpr (CT) b.v[0] *= cf.ay;
           As[obase + j * ARS * NL] = a;
           Bs[obase + j * ARS * NL] = b;
         }
       };
-      if constexpr (TL::NYI * CH <= NTHR) {
+      if constexpr (TL::NYI * CH == NTHR) {
+        phase_y(y_ibase, y_obase);
+      } else if constexpr (TL::NYI * CH <= NTHR) {
         if (tid < TL::NYI * CH) phase_y(y_ibase, y_obase);
       } else {
 #pragma unroll 1
@@ -490,28 +514,31 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
           }
 #pragma unroll
           for (int j = 0; j < P; ++j) {
-            S1 u, v;
+            S1 u, v, vk;   // (CT: v gathers M1 sig b, vk gathers K1 sig a, scaled by ax)
             u.zero();
             v.zero();
+            vk.zero();
+            S1& vka = CT ? vk : v;
 #pragma unroll
             for (int kk = 0; kk <= P; ++kk) {
-              u.fma(cf.AxM[j][kk], ao[kk]);
-              v.fma(cf.AxK[j][kk], ao[kk]);
-              v.fma(cf.AxM[j][kk], bo[kk]);
+              u.fma(cXM(j, kk), ao[kk]);
+              vka.fma(cXK(j, kk), ao[kk]);
+              v.fma(cXM(j, kk), bo[kk]);
             }
             if (j == 0) {
 #pragma unroll
               for (int kk = 0; kk < P; ++kk) {
                 const S1 ap = arow[kk * NL];
                 const S1 bp = brow[kk * NL];
-                u.fma(cf.AxM[P][kk], ap);
-                v.fma(cf.AxK[P][kk], ap);
-                v.fma(cf.AxM[P][kk], bp);
+                u.fma(cXM(P, kk), ap);
+                vka.fma(cXK(P, kk), ap);
+                v.fma(cXM(P, kk), bp);
               }
-              u.fma(cf.AxM[P][P], ao[0]);
-              v.fma(cf.AxK[P][P], ao[0]);
-              v.fma(cf.AxM[P][P], bo[0]);
+              u.fma(cXM(P, P), ao[0]);
+              vka.fma(cXK(P, P), ao[0]);
+              v.fma(cXM(P, P), bo[0]);
             }
+            if constexpr (CT) v.fma(cf.ax, vk);
             W1s[obase + j * NL] = u;
             W2s[obase + j * NL] = v;
           }
@@ -562,6 +589,12 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
 // 1D grid, vector tile fastest: the CTAs that read the other halves of a node's DRAM
 // bursts (neighbouring vector tiles of the same xy block) run side by side, so a burst is
 // fetched once; neighbouring xy blocks (halo sharing) follow within the resident window.
+// the float block operator (four-lane chunks) takes the compile-time shape tables
+template <typename T, int CH>
+struct KronShapeTables {
+  static constexpr bool value = std::is_same<T, float>::value && CH == 4;
+};
+
 // Residency bound: the float operator's tiles of up to 256 threads are held to three CTAs per
 // SM (at most 85 registers), where the per-plane barriers of one CTA overlap two others' work.
 template <typename T, int CH, class TL>
@@ -569,19 +602,19 @@ struct KronMinBlocks {
   static constexpr int value = (std::is_same<T, float>::value && CH == 4 && TL::NTHR <= 256) ? 3 : 1;
 };
 
-template <typename T, int CH, class TL, bool FULL>
+template <typename T, int CH, class TL, bool FULL, bool CT>
 __global__ void __launch_bounds__(TL::NTHR, (KronMinBlocks<T, CH, TL>::value))
 kron_kernel(const KronCoefT<T> cf, const KronGeom g, const KronIO<T> io, int nvt) {
   const int b = blockIdx.x;
   const int nxy = g.nbx * g.nby;
   const int r = b / nvt;
-  kron_body<T, CH, TL, FULL>(cf, g, io, r % nxy, b % nvt, r / nxy);
+  kron_body<T, CH, TL, FULL, CT>(cf, g, io, r % nxy, b % nvt, r / nxy);
 }
 
 // Batched form: many independent meshes that share p and the cell size (so one coefficient
 // table) in one launch.  The 1D grid concatenates the instances' CTA grids; a CTA finds its
 // instance by binary search over the ascending first-CTA offsets.
-template <typename T, int CH, class TL, bool FULL>
+template <typename T, int CH, class TL, bool FULL, bool CT>
 __global__ void __launch_bounds__(TL::NTHR, (KronMinBlocks<T, CH, TL>::value))
 kron_batch_kernel(const KronCoefT<T> cf, const KronInst<T>* __restrict__ inst, int ninst) {
   const int64_t b = blockIdx.x;
@@ -596,7 +629,7 @@ kron_batch_kernel(const KronCoefT<T> cf, const KronInst<T>* __restrict__ inst, i
   const int nxy = g.nbx * g.nby;
   const int64_t nvt = inst[lo].nvt;
   const int64_t r = local / nvt;
-  kron_body<T, CH, TL, FULL>(cf, g, io, (int)(r % nxy), (int)(local % nvt), (int)(r / nxy));
+  kron_body<T, CH, TL, FULL, CT>(cf, g, io, (int)(r % nxy), (int)(local % nvt), (int)(r / nxy));
 }
 
 // Dynamic shared memory limit, and the largest shared-memory carveout so that the residency
@@ -636,7 +669,10 @@ fe_status kron_launch_t(const KronCoef& cf, const KronGeom& g, const KronIO<T>& 
   if (smem > 227 * 1024) return fe_fail(FE_EINVAL, "tile needs %zu bytes of shared memory", smem);
   const int64_t vtile = (int64_t)TL::NCH * CH;
   const bool full = g.NX % TL::BXn == 0 && g.NY % TL::BYn == 0 && io.nvec % vtile == 0;
-  auto kern = full ? kron_kernel<T, CH, TL, true> : kron_kernel<T, CH, TL, false>;
+  auto kern = full ? kron_kernel<T, CH, TL, true, false> : kron_kernel<T, CH, TL, false, false>;
+  if constexpr (KronShapeTables<T, CH>::value) {
+    if (cf.mass_scale) kern = full ? kron_kernel<T, CH, TL, true, true> : kron_kernel<T, CH, TL, false, true>;
+  }
   FE_TRY(kron_func_setup(kern, smem));
   const int64_t nvt = (io.nvec + vtile - 1) / vtile;
   const int64_t total = (int64_t)g.nbx * g.nby * nvt * ((g.nz + g.zseg - 1) / g.zseg);
@@ -740,7 +776,11 @@ fe_status kron_batch_launch_t(const KronCoef& cf, const KronInst<T>* d_inst, int
   const size_t smem = kron_smem<T, CH, TL>(use_z, true);
   if (smem > 227 * 1024) return fe_fail(FE_EINVAL, "tile needs %zu bytes of shared memory", smem);
   if (total < 1 || total > 0x7fffffffLL) return fe_fail(FE_EINVAL, "batched grid of %lld CTAs", (long long)total);
-  auto kern = full ? kron_batch_kernel<T, CH, TL, true> : kron_batch_kernel<T, CH, TL, false>;
+  auto kern = full ? kron_batch_kernel<T, CH, TL, true, false> : kron_batch_kernel<T, CH, TL, false, false>;
+  if constexpr (KronShapeTables<T, CH>::value) {
+    if (cf.mass_scale)
+      kern = full ? kron_batch_kernel<T, CH, TL, true, true> : kron_batch_kernel<T, CH, TL, false, true>;
+  }
   FE_TRY(kron_func_setup(kern, smem));
   KronCoefT<T> cft = convert_coef<T>(cf);
   kern<<<(unsigned)total, TL::NTHR, smem, st>>>(cft, d_inst, n); fe_count_launch();

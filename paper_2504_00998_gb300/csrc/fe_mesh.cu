@@ -140,6 +140,8 @@ static void build_coef(fe_mesh* m, bool hamiltonian, KronCoef* c) {
       c->AzM[j][k] = m->M1[j][k];
     }
   for (int k = 0; k < n1; ++k) { c->sig[k] = sig[k]; c->wz[k] = m->w[k]; }
+  c->ax = ax;
+  c->ay = ay;
   c->mass_scale = hamiltonian ? 1 : 0;
   c->zin = hamiltonian ? 1.0 / std::sqrt(m->J) : 1.0;
   c->zout = hamiltonian ? 0.5 / std::sqrt(m->J) : 1.0;
