@@ -70,7 +70,13 @@ def test_apply_H_f64_matches_oracle(fe, L, ncell, p, dirichlet, nvec, ld):
         assert torch.all(ybuf[:, nvec:] == 7.0)
 
 
-@pytest.mark.parametrize("L,ncell,p,dirichlet", CASES[:6])
+# float block operator: the cases above plus a p = 5 mesh whose cells have three different
+# edge lengths (the in-plane scales ax, ay and az all differ and none is 1) and a full 4 x 4
+# cell tile in x and y
+F32_CASES = CASES[:6] + [((9.0, 6.0, 14.0), (4, 4, 5), 5, (True, True))]
+
+
+@pytest.mark.parametrize("L,ncell,p,dirichlet", F32_CASES)
 @pytest.mark.parametrize("nvec,ld", [(3, 4), (37, 40), (64, 64)])
 def test_apply_H_f32_matches_oracle(fe, L, ncell, p, dirichlet, nvec, ld):
     om, H, m, rng = _setup(fe, L, ncell, p, dirichlet, seed=1)
