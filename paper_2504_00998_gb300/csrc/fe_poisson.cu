@@ -681,49 +681,47 @@ __global__ void k_coarse_apply4(const double* __restrict__ seg, int nseg,
   }
 }
 
-// r -= mean (the state's, CEF); z = Dinv r + yf[plane] on free nodes; r.z and r.r partials; the
-// last block finishes beta, r.z, |r|^2, the iteration count and the convergence test
-__global__ void k_precond4_beta(float* __restrict__ r, float* __restrict__ z,
-                                const float* __restrict__ dinv,
-                                const unsigned char* __restrict__ mask, CgState* s, int project,
-                                int64_t n4, double* __restrict__ part_rz,
-                                double* __restrict__ part_rr, const float* __restrict__ yf,
-                                uint32_t plane4) {
+// r -= mean (the state's, CEF); z = Dinv r + yf[plane] on free nodes; r.z and r.r partials
+// per plane segment (block b: segment b % nseg of plane b / nseg, so the coarse correction of
+// the block's plane is one value); the last block finishes beta, r.z, |r|^2, the iteration
+// count and the convergence test
+__global__ void k_precond4s_beta(float* __restrict__ r, float* __restrict__ z,
+                                 const float* __restrict__ dinv,
+                                 const unsigned char* __restrict__ mask, CgState* s, int project,
+                                 int64_t plane4, int nseg, int seglen,
+                                 double* __restrict__ part_rz, double* __restrict__ part_rr,
+                                 const float* __restrict__ yf) {
   const float mean = project ? (float)s->mean : 0.f;
+  const int pl = blockIdx.x / nseg, sg = blockIdx.x - pl * nseg;
+  const int64_t lo = (int64_t)pl * plane4 + (int64_t)sg * seglen;
+  const int64_t hi = min((int64_t)pl * plane4 + plane4, lo + seglen);
+  const float cv = yf[pl];
   float4* r4 = reinterpret_cast<float4*>(r);
   float4* z4 = reinterpret_cast<float4*>(z);
   const float4* d4 = reinterpret_cast<const float4*>(dinv);
   const uchar4* m4 = reinterpret_cast<const uchar4*>(mask);
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   float a1 = 0.f, a2 = 0.f;
-  for (int64_t q0 = g; q0 < n4; q0 += V4B * stride) {
+  for (int64_t k0 = lo + threadIdx.x; k0 < hi; k0 += V4B * (int64_t)blockDim.x) {
     float4 rv[V4B], dv[V4B];
     uchar4 mv[V4B];
-    float cv[V4B];
 #pragma unroll
     for (int u = 0; u < V4B; ++u) {
-      const int64_t k = q0 + u * stride;
-      if (k < n4) {
-        rv[u] = r4[k];
-        dv[u] = d4[k];
-        mv[u] = m4[k];
-        cv[u] = yf[(uint32_t)k / plane4];
-      }
+      const int64_t k = k0 + u * (int64_t)blockDim.x;
+      if (k < hi) { rv[u] = r4[k]; dv[u] = d4[k]; mv[u] = m4[k]; }
     }
 #pragma unroll
     for (int u = 0; u < V4B; ++u) {
-      const int64_t k = q0 + u * stride;
-      if (k >= n4) continue;
+      const int64_t k = k0 + u * (int64_t)blockDim.x;
+      if (k >= hi) continue;
       float4 ri = rv[u], zi;
       if (project) {
         ri.x -= mean; ri.y -= mean; ri.z -= mean; ri.w -= mean;
         r4[k] = ri;
       }
-      zi.x = mv[u].x ? 0.f : dv[u].x * ri.x + cv[u];
-      zi.y = mv[u].y ? 0.f : dv[u].y * ri.y + cv[u];
-      zi.z = mv[u].z ? 0.f : dv[u].z * ri.z + cv[u];
-      zi.w = mv[u].w ? 0.f : dv[u].w * ri.w + cv[u];
+      zi.x = mv[u].x ? 0.f : dv[u].x * ri.x + cv;
+      zi.y = mv[u].y ? 0.f : dv[u].y * ri.y + cv;
+      zi.z = mv[u].z ? 0.f : dv[u].z * ri.z + cv;
+      zi.w = mv[u].w ? 0.f : dv[u].w * ri.w + cv;
       z4[k] = zi;
       a1 += ri.x * zi.x + ri.y * zi.y + ri.z * zi.z + ri.w * zi.w;
       a2 += ri.x * ri.x + ri.y * ri.y + ri.z * ri.z + ri.w * ri.w;
@@ -1047,7 +1045,8 @@ struct CgBuf {
   const double* ccnt;
   double* csum;
   double* cy;
-  double* seg;                 // plane-segment sums of r (float path with the coarse space)
+  double* seg;                 // float path with the coarse space: plane-segment sums of r, then
+                               // the preconditioner's r.z and r.r partials (3 nz nseg doubles)
   float* cyf;                  // float coarse correction per plane
   int nseg;                    // segments per plane
 };
@@ -1158,8 +1157,10 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
         k_coarse_apply4<<<(nzp + 7) / 8, 256, sizeof(double) * nzp, st>>>(
             b.seg, b.nseg, b.ccnt, b.Ainv, b.s, project, nzp, 1.0 / (double)n, b.cyf);
         fe_count_launch();
-        k_precond4_beta<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(
-            b.r, b.z, b.dinv, b.mask, b.s, project, n4, b.pc, b.pd, b.cyf, (uint32_t)(plane / 4));
+        const int64_t nsegs = (int64_t)nzp * b.nseg;
+        k_precond4s_beta<<<nzp * b.nseg, 256, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project,
+                                                       plane / 4, b.nseg, seglen, b.seg + nsegs,
+                                                       b.seg + 2 * nsegs, b.cyf);
         fe_count_launch();
         k_update_p4<<<fe::grid_for(n4), 256, 0, st>>>(b.p, b.z, b.s, n4); fe_count_launch();
         return FE_OK;
@@ -1286,7 +1287,7 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   const int nseg = (mixed && plane_n % 4 == 0) ? (int)((plane_n / 4 + 1023) / 1024) : 0;
   size_t bytes = nd * sizeof(double) + nf * sizeof(float) + 64 +
                  (4 * fe::RED_BLOCKS + (size_t)nzp) * sizeof(double) + 2 * sizeof(CgState) + n + 256 +
-                 (size_t)nzp * nseg * sizeof(double) + (size_t)nzp * sizeof(float) + 256;
+                 3 * (size_t)nzp * nseg * sizeof(double) + (size_t)nzp * sizeof(float) + 256;
   FE_TRY(fe_ws(m, WS_CG, bytes, &wsp));
   double* f = (double*)wsp;
   double* dinv = f + n;
@@ -1304,7 +1305,7 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   CgState* sref = s + 1;
   unsigned char* mask = (unsigned char*)(sref + 1);
   double* segp = (double*)(((uintptr_t)(mask + n) + 255) & ~(uintptr_t)255);
-  float* cyf = (float*)(segp + (size_t)nzp * nseg);
+  float* cyf = (float*)(segp + 3 * (size_t)nzp * nseg);
   const int project = bc->kind == FE_BIAS_CEF;
   const double* rh = rho ? rho : m->d_rho;
   const int gb = fe::grid_for(n);
