@@ -182,15 +182,21 @@ def test_plane_coarse_space_same_solution_fewer_iterations(fe, kind):
 
 
 @pytest.mark.parametrize("kind", ["cef", "lcpd"])
-def test_mixed_refinement_matches_double_cg(fe, kind):
+@pytest.mark.parametrize("layout", ["planes4", "odd_planes", "jacobi_only"])
+def test_mixed_refinement_matches_double_cg(fe, kind, layout):
     """Float corrections refined against the double residual reach the double CG's
     solution: same stopping test, solutions within the residual bound times the
-    conditioning (1e-9 relative)."""
-    base = W.small_slab(ncell=(3, 3, 12), p=4, L=(6.0, 6.0, 24.0), natoms=5, seed=17)
+    conditioning (1e-9 relative).  Three float iterations are covered: the fused one (planes of
+    a multiple of four nodes, plane coarse space), the scalar one (81-node planes) and the
+    four-node one without the coarse space (Jacobi only)."""
+    p = 3 if layout == "odd_planes" else 4
+    base = W.small_slab(ncell=(3, 3, 12), p=p, L=(6.0, 6.0, 24.0), natoms=5, seed=17)
     bias = {"cef": W.Bias("cef", field=0.01),
             "lcpd": W.Bias("cpd", dV=0.05, zA=2.0, zB=22.0, patch=((1.0, 1.0), (4.0, 5.0)))}[kind]
     slab = W.Slab(base.name, base.L, base.ncell, base.p, base.R, base.Z, bias)
     m = fe.Mesh.from_slab(slab)
+    if layout == "jacobi_only":
+        m.set_poisson_precond(False)
     out = {}
     for mixed in (False, True):
         m.set_poisson_mixed(mixed)
