@@ -129,9 +129,6 @@ fe_status kron_f32(const KronCoef& cf, const KronGeom& g, const KronIO<float>& i
                    cudaStream_t st);
 fe_status kron_k1(const KronCoef& cf, const KronGeom& g, const KronIO<double>& io,
                   cudaStream_t st);
-// float with one element per node (the corrections of the mixed-precision Poisson solve)
-fe_status kron_k1f(const KronCoef& cf, const KronGeom& g, const KronIO<float>& io,
-                   cudaStream_t st);
 // Batched launches: plan fills the tile fields, z segmentation, nvt and cta0 of n host
 // instances (g from fe_geom, io.nvec set) and returns the total CTA count; launch runs one
 // operator application over the device copy of those instances.
