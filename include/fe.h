@@ -243,6 +243,17 @@ fe_status fe_density(fe_mesh* mesh, const void* X, int64_t nvec, int64_t ld,
 fe_status fe_occupations(const double* eig_host, int n, double n_electrons, double kT,
                          double* occ_host, double* mu);
 
+/* Local-density exchange for the self-consistent potential (Section 2.1: the exchange-
+ * correlation potential enters V_eff as dE_xc/drho; this optional term is the closed-form
+ * exchange of the homogeneous electron gas, spin unpolarised, without correlation — a
+ * simplification of the paper's functional).  For the density rho_dev [n_phi] (values
+ * below zero taken as zero): adds v_x = -(3/pi)^(1/3) rho^(1/3) at the psi nodes to
+ * veff_dev [n_psi] in place (may be NULL), and writes E_x = sum_I M_II e_x(rho_I),
+ * e_x = -(3/4)(3/pi)^(1/3) rho^(4/3), to *ex_host (may be NULL; the call then synchronises
+ * the mesh stream).  FE_EINVAL for a null mesh or density. */
+fe_status fe_lda_exchange(fe_mesh* mesh, const double* rho_dev, double* veff_dev,
+                          double* ex_host);
+
 /* Anderson / Pulay mixing of phi-node densities (D. G. Anderson 1965, P. Pulay 1980) with
  * the lumped-mass inner product: with R = rho_out - rho_in and the differences dR_i,
  * drho_i of the last `history` (0..16) steps, gamma minimises |R - sum gamma_i dR_i| and

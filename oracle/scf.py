@@ -18,9 +18,16 @@ the benchmark's CPU baseline may import it; the library never does.
   gamma minimises |R - sum_i gamma_i dR_i| and
   rho_next = rho_in + alpha R - sum_i gamma_i (drho_i + alpha dR_i); with m = 0 this is
   linear mixing rho_next = rho_in + alpha R.
-* One self-consistent iteration (Hartree level, no exchange-correlation, which is out of
-  the computed path): Poisson solve with the bias, V_eff, Chebyshev-filtered subspace
-  iteration, occupations, rho_out, mixing.
+* One self-consistent iteration: Poisson solve with the bias, V_eff, Chebyshev-filtered
+  subspace iteration, occupations, rho_out, mixing.  Hartree level by default; optionally
+  with local-density exchange (reading: the paper's exchange-correlation functional enters
+  V_eff through v_xc = dE_xc/drho, Section 2.1; its GGA needs a functional library, so the
+  optional term here is the closed-form exchange of the homogeneous electron gas, Dirac
+  1930, spin unpolarised, no correlation):
+      e_x(rho) = -(3/4) (3/pi)^(1/3) rho^(4/3)   (energy per volume),
+      v_x(rho) = d e_x / d rho = -(3/pi)^(1/3) rho^(1/3),
+  negative densities (possible after mixing) taken as zero; E_x = sum_I M_II e_x(rho_I)
+  in the lumped quadrature, v_x added to V_eff at the psi nodes.
 """
 import math
 
@@ -38,6 +45,14 @@ def density_phi(X, occ, M, psi_ids):
     rho = np.zeros(M.shape[0])
     rho[psi_ids] = density(X, occ, M[psi_ids])
     return rho
+
+
+def lda_exchange(rho):
+    """(e_x, v_x) of the Dirac exchange at each value of rho (see the module text)."""
+    r = np.maximum(np.asarray(rho, dtype=np.float64), 0.0)
+    c = (3.0 / math.pi) ** (1.0 / 3.0)
+    cbrt = np.cbrt(r)
+    return -0.75 * c * r * cbrt, -c * cbrt
 
 
 def fermi(eps, mu, kT):
@@ -101,7 +116,7 @@ class AndersonMixer:
 
 
 def scf_run(slab, X0, iters, kT=0.01, alpha=0.3, history=4, degree=None, first_cycles=4,
-            lanczos_steps=20, v0=None):
+            lanczos_steps=20, v0=None, xc=None):
     """Hartree-level self-consistent iterations on a small slab, every step in FP64.
 
     Per iteration k: phi from the Poisson problem with the load 4 pi M (rho_in + b) and the
@@ -109,8 +124,9 @@ def scf_run(slab, X0, iters, kT=0.01, alpha=0.3, history=4, degree=None, first_c
     of Ht; filter + Rayleigh-Ritz cycles (first_cycles at k = 0, one afterwards) with
     a0 = lo, b = hi and the cut a = a0 + 0.1 (b - a0) for the very first cycle, else the
     largest Ritz value of the previous cycle; occupations and mu; rho_out; Anderson mixing.
-    The first rho_in is the atoms' model density.  Returns a dict with the final rho_in,
-    mu, Ritz values, block and the residual norms of every iteration."""
+    The first rho_in is the atoms' model density.  xc = "lda_x" adds v_x(rho_in) to V_eff.
+    Returns a dict with the final rho_in, mu, Ritz values, block and the residual norms of
+    every iteration (and E_x of the last rho_in with xc)."""
     from oracle import assembly, chefsi, poisson, potentials
     from oracle.mesh import Mesh as OMesh
     om = OMesh(slab.L, slab.ncell, slab.p, slab.psi_dirichlet)
@@ -140,6 +156,8 @@ def scf_run(slab, X0, iters, kT=0.01, alpha=0.3, history=4, degree=None, first_c
         else:
             phi = poisson.solve_cpd_direct(K, f, mask, vals)
         V = (phi + vl + vapp)[ids]
+        if xc == "lda_x":
+            V = V + lda_exchange(rho_in)[1][ids]
         H = assembly.hamiltonian(om, V, K, M)
         lo, hi = chefsi.lanczos_bounds(lambda v: H @ v, v0, lanczos_steps)
         for _ in range(first_cycles if k == 0 else 1):
@@ -150,4 +168,7 @@ def scf_run(slab, X0, iters, kT=0.01, alpha=0.3, history=4, degree=None, first_c
         rho_out = density_phi(Xb, occ, M, ids)
         rho_in, r = mixer.step(rho_in, rho_out)
         res.append(r)
-    return {"rho": rho_in, "mu": mu, "eig": eig, "X": Xb, "res": res, "M": M}
+    out = {"rho": rho_in, "mu": mu, "eig": eig, "X": Xb, "res": res, "M": M}
+    if xc == "lda_x":
+        out["ex"] = float(M @ lda_exchange(rho_in)[0])
+    return out

@@ -13,7 +13,7 @@
 
 #define FE_MAXP 6
 #define FE_MAXN1 (FE_MAXP + 1)
-#define FE_NWS 14   // workspace slots of a mesh
+#define FE_NWS 15   // workspace slots of a mesh
 
 // ---- error state ------------------------------------------------------------------------
 fe_status fe_fail(fe_status st, const char* fmt, ...);
@@ -216,7 +216,7 @@ struct fe_mesh {
 
 enum { WS_CHEB = 0, WS_RR_X = 1, WS_RR_HX = 2, WS_RR_SMALL = 3, WS_CG = 4, WS_RED = 5,
        WS_LANCZOS = 6, WS_TC = 7, WS_TC_IMG = 8, WS_YCELL = 9, WS_RR_TC32 = 10,
-       WS_PCOARSE = 11, WS_NL = 12, WS_KCELL = 13 };
+       WS_PCOARSE = 11, WS_NL = 12, WS_KCELL = 13, WS_XC = 14 };
 
 fe_status fe_ws(fe_mesh* m, int slot, size_t bytes, void** out);
 // single-vector float stiffness product through cell-local products (fe_kcell.cu); its

@@ -5,6 +5,9 @@
 // blocks hold xt_n = M^1/2 u_n (Euclidean-orthonormal columns of Ht = M^-1/2 H M^-1/2,
 // Section 2.3), so at psi node I, rho_I = sum_n occ_n xt_{I,n}^2 / M_II with occ_n = 2 f_n;
 // the homogeneous-Dirichlet z planes carry no psi node and get rho = 0.
+// Local-density exchange (Dirac, spin unpolarised; the optional exchange term of the
+// self-consistent potential): e_x = -(3/4)(3/pi)^(1/3) rho^(4/3) per volume,
+// v_x = -(3/pi)^(1/3) rho^(1/3), negative densities taken as zero.
 // Occupations: Fermi-Dirac at smearing temperature kT, mu by bisection on
 // 2 sum_n f_n = N_e.  Mixing: Anderson (J. ACM 12, 1965) / Pulay (Chem. Phys. Lett. 73,
 // 1980) on the density with the lumped-mass inner product.
@@ -15,6 +18,21 @@
 #include "fe_internal.h"
 
 namespace {
+
+// e_x at every phi node (for the lumped-mass sum) and veff += v_x at the psi nodes
+__global__ void k_lda_exchange(const double* __restrict__ rho, double* __restrict__ ex,
+                               double* __restrict__ veff, int64_t off, int64_t npsi,
+                               int64_t nphi) {
+  const double c = 0.98474502184269641;   // (3/pi)^(1/3)
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nphi;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double r = rho[i] > 0.0 ? rho[i] : 0.0;
+    const double cr = cbrt(r);
+    ex[i] = -0.75 * c * r * cr;
+    const int64_t j = i - off;
+    if (veff && j >= 0 && j < npsi) veff[j] += -c * cr;
+  }
+}
 
 // one warp per psi node: lanes stride over the vectors
 template <typename T>
@@ -357,5 +375,27 @@ extern "C" fe_status fe_mixer_step(fe_mixer* x, double* rho_in, const double* rh
   fe_count_launch();
   FE_CUDA(cudaGetLastError());
   if (resid_norm) *resid_norm = std::sqrt(std::fmax(rr, 0.0));
+  return FE_OK;
+}
+
+extern "C" fe_status fe_lda_exchange(fe_mesh* m, const double* rho, double* veff,
+                                     double* ex_host) {
+  if (!m || !rho) return fe_fail(FE_EINVAL, "fe_lda_exchange: null argument");
+  FE_TRY(fe_activate(m));
+  const int64_t n = m->n_phi;
+  void* wsp = nullptr;
+  FE_TRY(fe_ws(m, WS_XC, sizeof(double) * ((size_t)n + fe::RED_BLOCKS + 8), &wsp));
+  double* ex = static_cast<double*>(wsp);
+  double* part = ex + n;
+  double* out = part + fe::RED_BLOCKS;
+  const int64_t off = (int64_t)m->gz_lo * m->NX * m->NY;
+  k_lda_exchange<<<fe::grid_for(n), 256, 0, m->stream>>>(rho, ex, veff, off, m->n_psi, n);
+  fe_count_launch();
+  FE_CUDA(cudaGetLastError());
+  if (ex_host) {
+    FE_TRY(fe::dot_async(m->d_mass, ex, n, 1, part, out, m->stream));
+    FE_CUDA(cudaMemcpyAsync(ex_host, out, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    FE_CUDA(cudaStreamSynchronize(m->stream));
+  }
   return FE_OK;
 }

@@ -1,5 +1,6 @@
-"""Self-consistent iterations of the slab (Hartree level: no exchange-correlation) driven
-through libfe: Poisson with the bias (fe_poisson_solve with the current density), V_eff,
+"""Self-consistent iterations of the slab driven through libfe (Hartree level, optionally
+with local-density exchange, fe_lda_exchange): Poisson with the bias (fe_poisson_solve with
+the current density), V_eff,
 Lanczos bounds, Chebyshev-filtered subspace iteration, Fermi-Dirac occupations
 (fe_occupations), the density of the block (fe_density) and Anderson mixing
 (fe_mixer_step).  Every step runs in the library; this module only sequences the calls.
@@ -49,6 +50,15 @@ def occupations(eig, n_electrons, kT):
     return occ, mu.value
 
 
+def lda_exchange(mesh, rho, veff=None):
+    """E_x of the phi-node density rho (fe_lda_exchange); adds v_x to veff (psi nodes, in
+    place) when given."""
+    ex = C.c_double()
+    call("fe_lda_exchange", mesh.handle, C.c_void_p(rho.data_ptr()),
+         C.c_void_p(veff.data_ptr()) if veff is not None else None, C.byref(ex))
+    return ex.value
+
+
 def density(mesh, X, occ, prec):
     """rho on phi nodes from the block X and occupations occ (device or host)."""
     o = torch.as_tensor(occ, dtype=torch.float64).to(X.device).contiguous()
@@ -59,14 +69,18 @@ def density(mesh, X, occ, prec):
 
 
 def scf_run(mesh, bias, n_electrons, X, iters, kT=0.01, alpha=0.3, history=4, degree=10,
-            first_cycles=4, lanczos_steps=20, v0=None, prec=0, rtol=1e-12, max_iter=50000):
+            first_cycles=4, lanczos_steps=20, v0=None, prec=0, rtol=1e-12, max_iter=50000,
+            xc=None):
     """Self-consistent iterations from the atoms' model density (the same sequence as the
     CPU oracle's scf_run): per iteration the Poisson solve with the load 4 pi M (rho_in + b)
     and the bias, V_eff, Lanczos bounds (lo, hi) from v0, filter + Rayleigh-Ritz cycles
     (first_cycles on the first iteration, then one) with a0 = lo, b = hi and the cut
     a = lo + 0.1 (hi - lo) for the very first cycle, else the previous largest Ritz value;
-    occupations, rho_out, Anderson mixing.  X (the block, updated in place) holds the
-    start vectors.  Returns dict(rho, mu, eig, res)."""
+    occupations, rho_out, Anderson mixing.  xc = "lda_x" adds the local-density exchange
+    potential of rho_in to V_eff.  X (the block, updated in place) holds the start vectors.
+    Returns dict(rho, mu, eig, res) (and ex, E_x of the final rho_in, with xc)."""
+    if xc not in (None, "lda_x"):
+        raise ValueError("xc must be None or 'lda_x'")
     dev = X.device
     rho_in, _, _ = mesh.atom_fields()
     rho_in = rho_in.clone()
@@ -76,6 +90,8 @@ def scf_run(mesh, bias, n_electrons, X, iters, kT=0.01, alpha=0.3, history=4, de
     try:
         for k in range(iters):
             _, vbare, _ = mesh.poisson_solve(bias, rho=rho_in, rtol=rtol, max_iter=max_iter)
+            if xc == "lda_x":
+                lda_exchange(mesh, rho_in, vbare)
             mesh.set_potential(vbare)
             lo, hi = mesh.lanczos_bounds(v0, lanczos_steps)
             for _ in range(first_cycles if k == 0 else 1):
@@ -88,4 +104,7 @@ def scf_run(mesh, bias, n_electrons, X, iters, kT=0.01, alpha=0.3, history=4, de
             res.append(mixer.step(rho_in, rho_out))
     finally:
         mixer.close()
-    return {"rho": rho_in, "mu": mu, "eig": eig, "res": res}
+    out = {"rho": rho_in, "mu": mu, "eig": eig, "res": res}
+    if xc == "lda_x":
+        out["ex"] = lda_exchange(mesh, rho_in)
+    return out

@@ -89,3 +89,47 @@ def test_scf_run_matches_oracle(fe, kind):
     # the density of the converging run keeps the electron count
     M = ref["M"]
     assert abs(float(M @ rho) - float(np.sum(slab.Z))) <= 1e-9 * float(np.sum(slab.Z))
+
+
+def test_lda_exchange_matches_oracle(fe):
+    """fe_lda_exchange against the oracle: v_x added at the psi nodes and E_x (lumped sum),
+    1e-12 relative, on a density with negative entries (taken as zero on both sides)."""
+    from paper_2504_00998_gb300 import scf as fscf
+    slab = W.small_slab(ncell=(3, 2, 5), p=3, L=(6.0, 4.0, 12.0), natoms=3, seed=9)
+    om = OMesh(slab.L, slab.ncell, slab.p, slab.psi_dirichlet)
+    M = assembly.lumped_mass(om)
+    rng = np.random.default_rng(4)
+    rho = rng.uniform(-0.01, 0.5, om.n_phi)
+    v0 = rng.uniform(-1.0, 1.0, om.n_psi)
+    m = fe.Mesh.from_slab(slab)
+    veff = torch.tensor(v0, device="cuda")
+    ex = fscf.lda_exchange(m, torch.tensor(rho, device="cuda"), veff)
+    ex_ref, vx_ref = scf.lda_exchange(rho)
+    np.testing.assert_allclose(veff.cpu().numpy(), v0 + vx_ref[om.psi_to_phi()], rtol=1e-12, atol=1e-14)
+    assert abs(ex - float(M @ ex_ref)) <= 1e-12 * abs(float(M @ ex_ref))
+
+
+def test_scf_run_with_lda_exchange_matches_oracle(fe):
+    """The self-consistent run with the exchange term: same Ritz values, mu, density and E_x
+    as the oracle's run; exchange lowers the occupied levels against the Hartree-level run."""
+    from paper_2504_00998_gb300 import scf as fscf
+    bias = W.Bias("cef", field=0.01)
+    base = W.small_slab(ncell=(2, 2, 6), p=3, L=(4.0, 4.0, 14.0), natoms=4, seed=3, nvec=16,
+                        degree=8)
+    slab = W.Slab(base.name, base.L, base.ncell, base.p, base.R, base.Z, bias, nvec=16, degree=8,
+                  seed=base.seed)
+    X0 = W.start_block(slab).astype(np.float64)
+    iters = 6
+    ref = scf.scf_run(slab, X0, iters=iters, xc="lda_x")
+    ref_h = scf.scf_run(slab, X0, iters=iters)
+    m = fe.Mesh.from_slab(slab)
+    X = torch.tensor(X0, device="cuda")
+    out = fscf.scf_run(m, bias, float(np.sum(slab.Z)), X, iters=iters, degree=8, prec=fe.FE_F64,
+                       xc="lda_x")
+    assert abs(out["mu"] - ref["mu"]) <= 1e-7
+    assert np.max(np.abs(out["eig"] - ref["eig"])) <= 1e-7
+    rho = out["rho"].cpu().numpy()
+    assert np.max(np.abs(rho - ref["rho"])) <= 1e-7 * np.max(np.abs(ref["rho"]))
+    assert abs(out["ex"] - ref["ex"]) <= 1e-7 * abs(ref["ex"])
+    assert ref["ex"] < 0.0
+    assert ref["eig"][0] < ref_h["eig"][0]

@@ -81,3 +81,44 @@ def test_anderson_solves_a_linear_fixed_point_problem():
 
     assert run(8, 100) <= 1e-12 * np.linalg.norm(xstar)
     assert run(0, 100) >= 1e-3 * np.linalg.norm(xstar)
+
+
+def test_lda_exchange_matches_the_homogeneous_gas():
+    """Exchange energy per electron of the homogeneous gas at Wigner-Seitz radius r_s:
+    -(3/4) (9 / (4 pi^2))^(1/3) / r_s = -0.458165... / r_s Ha (textbook constant, written
+    here in r_s rather than rho)."""
+    for rs in (0.5, 1.0, 2.0, 5.0):
+        rho = 3.0 / (4.0 * np.pi * rs ** 3)
+        ex, _ = scf.lda_exchange(np.array([rho]))
+        assert abs(ex[0] / rho - (-0.4581652932831429 / rs)) <= 1e-14 / rs
+
+
+def test_lda_exchange_potential_is_the_derivative_and_scales():
+    rho = np.array([1e-4, 0.01, 0.3, 2.0, 7.5])
+    ex, vx = scf.lda_exchange(rho)
+    h = 1e-6 * rho
+    fd = (scf.lda_exchange(rho + h)[0] - scf.lda_exchange(rho - h)[0]) / (2 * h)
+    np.testing.assert_allclose(vx, fd, rtol=1e-8)
+    lam = 3.7
+    np.testing.assert_allclose(scf.lda_exchange(lam * rho)[0], lam ** (4.0 / 3.0) * ex, rtol=1e-14)
+    np.testing.assert_allclose(scf.lda_exchange(lam * rho)[1], lam ** (1.0 / 3.0) * vx, rtol=1e-14)
+    ex0, vx0 = scf.lda_exchange(np.array([0.0, -1e-9]))
+    assert np.all(ex0 == 0.0) and np.all(vx0 == 0.0)
+
+
+def test_lda_exchange_energy_of_a_gaussian_density():
+    """E_x of a normalised Gaussian density of width s: the integral of rho^(4/3) is
+    (2 pi s^2)^(-1/2) (3/4)^(3/2) for one electron, so E_x = -(3/4)(3/pi)^(1/3) times that;
+    the lumped quadrature on a fine p = 4 mesh reproduces it."""
+    from oracle.mesh import Mesh as OMesh
+    from oracle import assembly
+    s_w = 0.8
+    L = (8.0, 8.0, 8.0)
+    om = OMesh(L, (8, 8, 8), 4, (False, False))
+    X = om.phi_coords()
+    M = assembly.lumped_mass(om)
+    r2 = np.sum((X - 4.0) ** 2, axis=1)
+    rho = np.exp(-r2 / (2 * s_w ** 2)) / (2 * np.pi * s_w ** 2) ** 1.5
+    ex = float(M @ scf.lda_exchange(rho)[0])
+    exact = -0.75 * (3 / np.pi) ** (1 / 3) * (2 * np.pi * s_w ** 2) ** -0.5 * (3 / 4) ** 1.5
+    assert abs(ex - exact) <= 1e-6 * abs(exact)
