@@ -42,9 +42,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--prec", choices=["f32", "f64", "bf16"], default="f32")
-    ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep"], default="p5",
+    ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep", "p5nl", "scf"],
+                    default="p5",
                     help="p5: the benchmark slab; p5s / p3: smaller slabs; sweep: the batched "
-                         "bias sweep of 24 independent 8x8xH-cell p=4 slabs")
+                         "bias sweep of 24 independent 8x8xH-cell p=4 slabs; p5nl: the "
+                         "benchmark step with synthetic nonlocal projectors on every atom; "
+                         "scf: self-consistent iterations on the benchmark slab")
     ap.add_argument("--rr", choices=["f64", "tc32"], default="tc32",
                     help="Rayleigh-Ritz block products for float storage: double GEMMs or "
                          "FP32-accurate tensor-core emulation (n x n part always double)")
@@ -56,7 +59,7 @@ def parse():
 def workload(name):
     """p5: the benchmark slab; p5s: the same p = 5 cells and vectors with 16 cell layers and
     256 vectors (a 0.5 GB block, above L2) for profiler captures; p3: the small CEF slab."""
-    if name == "p5":
+    if name in ("p5", "p5nl", "scf"):
         return W.config2()
     if name == "p5s":
         s = W.config2()
@@ -303,6 +306,13 @@ def run_gpu(args):
     m = fe.Mesh.from_slab(slab, device=local)
     if prec != fe.FE_F64:
         m.set_rr_products(args.rr == "tc32")
+    nl_desc = ""
+    if args.workload == "p5nl":
+        # synthetic s + p projectors on every atom (the stand-in for the pseudopotentials'
+        # nonlocal part): width 0.8 bohr, cut at 2.6 bohr, D = (1.0, 0.4, 0.4, 0.4) Ha
+        na = len(slab.R)
+        m.set_nonlocal(slab.R, np.full(na, 0.8), np.tile([1.0, 0.4, 0.4, 0.4], (na, 1)), 2.6)
+        nl_desc = f" + synthetic s,p nonlocal projectors on all {na} atoms (sigma 0.8, cut 2.6 bohr)"
     phi = torch.empty(m.n_phi, dtype=torch.float64, device=dev)
     vb = torch.empty(m.n_psi, dtype=torch.float64, device=dev)
     m.poisson_solve(slab.bias, rtol=POISSON_RTOL, phi=phi, vbare=vb)
@@ -381,7 +391,8 @@ def run_gpu(args):
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_src = measured_peaks()
     kernel_key = {fe.FE_F32: "kron_f32_p5", fe.FE_F64: "kron_f64_p5"}.get(prec, "tc_p5")
-    traffic = traffic_record(kernel_key)
+    # (the nonlocal term adds its own kernels to the filter time: no single-kernel traffic)
+    traffic = traffic_record(kernel_key) if not nl_desc else None
 
     # end to end through the public API with host buffers: every step copies its input
     # block in from pinned host memory and reads its result (the Ritz values) back.  The
@@ -459,7 +470,7 @@ def run_gpu(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
-            "config": {"workload": workload_desc(slab),
+            "config": {"workload": workload_desc(slab) + nl_desc,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (block of %.1f GB)" % (n * nvec * eb / 1e9),
                        "rr_products": args.rr if prec != fe.FE_F64 else "f64",
@@ -589,12 +600,60 @@ def run_sweep(args):
     return 0
 
 
+def run_scf(args):
+    """Self-consistent iterations on the benchmark slab (Hartree level, CEF bias): the time
+    of one iteration (Poisson, V_eff, Lanczos bounds, one filter + Rayleigh-Ritz cycle,
+    occupations, density, Anderson mixing).  A run of 1 + K iterations and a run of one
+    iteration are timed (after warm-up runs); their difference over K excludes each run's
+    set-up (model density, mixer)."""
+    import torch
+    import paper_2504_00998_gb300 as fe
+    from paper_2504_00998_gb300 import scf as fscf
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    slab = W.config2()
+    m = fe.Mesh.from_slab(slab, device=0)
+    m.set_rr_products(True)
+    X = torch.tensor(W.start_block(slab), device=dev)
+    n_e = float(np.sum(slab.Z))
+    st = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(iters):
+        t0, t1 = ev(), ev()
+        torch.cuda.synchronize(dev)
+        t0.record(st)
+        out = fscf.scf_run(m, slab.bias, n_e, X, iters=iters, degree=slab.degree,
+                           prec=fe.FE_F32, rtol=POISSON_RTOL, first_cycles=1)
+        t1.record(st)
+        torch.cuda.synchronize(dev)
+        return t0.elapsed_time(t1), out
+
+    for _ in range(max(args.warmup, 1)):
+        timed(1)
+    t1_ms, _ = timed(1)
+    tk_ms, out = timed(1 + args.steps)
+    ms = (tk_ms - t1_ms) / args.steps
+    print(json.dumps({
+        "metric": "SCF iteration time", "value": ms, "unit": "ms", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(slab) + "; Hartree-level self-consistent iterations",
+                   "parallelism": "single GPU"},
+        "run_ms": {"1": t1_ms, str(1 + args.steps): tk_ms},
+        "mixing_residuals": out["res"], "mu": out["mu"]}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "scf":
+        return run_scf(args)
     return run_gpu(args)
 
 

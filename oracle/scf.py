@@ -123,7 +123,8 @@ def scf_run(slab, X0, iters, kT=0.01, alpha=0.3, history=4, degree=None, first_c
     slab's bias; V_eff = phi + V_loc - V_sm + V_app at psi nodes; Lanczos bounds (lo, hi)
     of Ht; filter + Rayleigh-Ritz cycles (first_cycles at k = 0, one afterwards) with
     a0 = lo, b = hi and the cut a = a0 + 0.1 (b - a0) for the very first cycle, else the
-    largest Ritz value of the previous cycle; occupations and mu; rho_out; Anderson mixing.
+    largest Ritz value of the previous cycle when it lies in (lo, hi) (else the first-cycle
+    rule again); occupations and mu; rho_out; Anderson mixing.
     The first rho_in is the atoms' model density.  xc = "lda_x" adds v_x(rho_in) to V_eff.
     Returns a dict with the final rho_in, mu, Ritz values, block and the residual norms of
     every iteration (and E_x of the last rho_in with xc)."""
@@ -161,7 +162,9 @@ def scf_run(slab, X0, iters, kT=0.01, alpha=0.3, history=4, degree=None, first_c
         H = assembly.hamiltonian(om, V, K, M)
         lo, hi = chefsi.lanczos_bounds(lambda v: H @ v, v0, lanczos_steps)
         for _ in range(first_cycles if k == 0 else 1):
-            a = lo + 0.1 * (hi - lo) if cut is None else cut
+            # the previous largest Ritz value when it lies inside the new interval, else
+            # the first-cycle rule (the potential can move the spectrum between iterations)
+            a = cut if cut is not None and lo < cut < hi else lo + 0.1 * (hi - lo)
             eig, Xb = chefsi.chefsi_cycle(lambda Z: H @ Z, Xb, degree, a, hi, lo)
             cut = eig[-1]
         occ, mu = occupations(eig, n_e, kT)

@@ -75,7 +75,8 @@ def scf_run(mesh, bias, n_electrons, X, iters, kT=0.01, alpha=0.3, history=4, de
     CPU oracle's scf_run): per iteration the Poisson solve with the load 4 pi M (rho_in + b)
     and the bias, V_eff, Lanczos bounds (lo, hi) from v0, filter + Rayleigh-Ritz cycles
     (first_cycles on the first iteration, then one) with a0 = lo, b = hi and the cut
-    a = lo + 0.1 (hi - lo) for the very first cycle, else the previous largest Ritz value;
+    a = lo + 0.1 (hi - lo) for the very first cycle, else the previous largest Ritz value
+    when it lies in (lo, hi) (else the first-cycle rule again);
     occupations, rho_out, Anderson mixing.  xc = "lda_x" adds the local-density exchange
     potential of rho_in to V_eff.  X (the block, updated in place) holds the start vectors.
     Returns dict(rho, mu, eig, res) (and ex, E_x of the final rho_in, with xc)."""
@@ -95,7 +96,9 @@ def scf_run(mesh, bias, n_electrons, X, iters, kT=0.01, alpha=0.3, history=4, de
             mesh.set_potential(vbare)
             lo, hi = mesh.lanczos_bounds(v0, lanczos_steps)
             for _ in range(first_cycles if k == 0 else 1):
-                a = lo + 0.1 * (hi - lo) if cut is None else cut
+                # the previous largest Ritz value when it lies inside the new interval, else
+                # the first-cycle rule (the potential can move the spectrum between iterations)
+                a = cut if cut is not None and lo < cut < hi else lo + 0.1 * (hi - lo)
                 mesh.cheb_filter(X, degree, a, hi, lo, prec=prec)
                 eig = mesh.rayleigh_ritz(X, prec=prec).cpu().numpy()
                 cut = float(eig[-1])
