@@ -143,6 +143,20 @@ fe_status fe_set_atoms(fe_mesh* mesh, int n, const double* R_host, const double*
 fe_status fe_set_nonlocal(fe_mesh* mesh, int natoms, const double* R_host,
                           const double* sigma_host, const double* D_host, double rc);
 
+/* Bloch wave vector (Section 2.1: Bloch's theorem along the periodic x and y directions,
+ * psi = e^{i k.x} u, H^k_loc = -1/2 Laplacian - i k.grad + 1/2 |k|^2 + V_eff on u).  With
+ * k = (kx, ky) != 0 the scaled operator becomes the Hermitian
+ * Ht_k = Ht_0 + |k|^2 / 2 - i M^-1/2 (kx Gx + ky Gy) M^-1/2 (G^d_IJ = int N_I dN_J/dx_d,
+ * exact; the |k|^2 term with the lumped overlap), and the blocks of fe_apply_H,
+ * fe_cheb_filter and fe_rayleigh_ritz are complex: interleaved (re, im) pairs of float
+ * (FE_F32) or double (FE_F64), nvec and ld counting complex entries (16-byte aligned rows).
+ * fe_rayleigh_ritz then solves the Hermitian subspace problem in double complex; fe_density
+ * sums occ_n |u_n|^2 over the complex columns; fe_lanczos_bounds bounds the spectrum of
+ * Ht_k.  k = (0, 0) restores the real Gamma-point operator.  Not combined with the nonlocal
+ * term, the tensor-core precisions, fe_batch_create or fe_cheb_filter_static
+ * (FE_EUNSUPPORTED).  FE_EINVAL for a null mesh or a non-finite k. */
+fe_status fe_set_kpoint(fe_mesh* mesh, double kx, double ky);
+
 /* V_eff at psi nodes, veff_dev[n_psi] (Eq. Veff and Hloc without exchange-correlation:
  * V_eff = phi + V_loc - V_sm + V_app).  Copied into the mesh. */
 fe_status fe_set_potential(fe_mesh* mesh, const double* veff_dev);

@@ -22,7 +22,8 @@ def cheb_filter(apply_H, X, m, a, b, a0):
     c = (b + a) / 2.0
     sigma = e / (a0 - c)
     tau = 2.0 / sigma
-    X = np.asarray(X, dtype=np.float64)
+    # real blocks in double; complex (Bloch) blocks in double complex, same recurrence
+    X = np.asarray(X, dtype=np.complex128 if np.iscomplexobj(X) else np.float64)
     Y = (sigma / e) * (apply_H(X) - c * X)
     for _ in range(2, m + 1):
         sigma_new = 1.0 / (tau - sigma)

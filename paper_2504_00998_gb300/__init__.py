@@ -18,7 +18,9 @@ __all__ = ["Mesh", "Batch", "FeError", "FE_F64", "FE_F32", "FE_BF16_F32ACC", "FE
 load = _lib.load
 
 
-def storage_dtype(prec):
+def storage_dtype(prec, complex_=False):
+    if complex_:
+        return torch.complex128 if prec == FE_F64 else torch.complex64
     return torch.float64 if prec == FE_F64 else torch.float32
 
 
@@ -138,20 +140,29 @@ class Mesh:
         Dt = torch.as_tensor(D, dtype=torch.float64).contiguous().cpu()
         call("fe_set_nonlocal", self._h, int(sg.numel()), _ptr(R), _ptr(sg), _ptr(Dt), float(rc))
 
+    def set_kpoint(self, kx, ky):
+        """Bloch wave vector (fe_set_kpoint); blocks are then complex tensors."""
+        call("fe_set_kpoint", self._h, float(kx), float(ky))
+        self.kpoint = (float(kx), float(ky))
+
+    def _block_dtype(self, prec):
+        k = getattr(self, "kpoint", (0.0, 0.0))
+        return storage_dtype(prec, complex_=(k != (0.0, 0.0)))
+
     def set_potential(self, veff):
         assert veff.dtype == torch.float64 and veff.is_cuda and veff.numel() == self.n_psi
         call("fe_set_potential", self._h, _ptr(veff.contiguous()))
 
     def apply_H(self, X, Y=None, prec=FE_F64):
         n, nvec = X.shape[0], X.shape[1]
-        assert n == self.n_psi and X.dtype == storage_dtype(prec) and X.is_cuda
+        assert n == self.n_psi and X.dtype == self._block_dtype(prec) and X.is_cuda
         if Y is None:
             Y = torch.empty_like(X)
         call("fe_apply_H", self._h, _ptr(X), _ptr(Y), nvec, X.stride(0), int(prec))
         return Y
 
     def cheb_filter(self, X, degree, a, b, a0, prec=FE_F64):
-        assert X.dtype == storage_dtype(prec) and X.shape[0] == self.n_psi
+        assert X.dtype == self._block_dtype(prec) and X.shape[0] == self.n_psi
         call("fe_cheb_filter", self._h, _ptr(X), X.shape[1], X.stride(0), int(degree), float(a),
              float(b), float(a0), int(prec))
         return X

@@ -189,9 +189,12 @@ extern "C" fe_status fe_batch_create(fe_mesh* const* meshes, int n, fe_batch** o
   for (int i = 0; i < n; ++i)
     if (!meshes[i]) return fe_fail(FE_EINVAL, "fe_batch_create: mesh %d is null", i);
   const fe_mesh* m0 = meshes[0];
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (meshes[i]->nl.natoms > 0)
       return fe_fail(FE_EUNSUPPORTED, "fe_batch_create: mesh %d carries the nonlocal term", i);
+    if (meshes[i]->has_k)
+      return fe_fail(FE_EUNSUPPORTED, "fe_batch_create: mesh %d has a Bloch wave vector", i);
+  }
   for (int i = 1; i < n; ++i) {
     const fe_mesh* m = meshes[i];
     if (m->device != m0->device || m->stream != m0->stream)

@@ -41,8 +41,34 @@ fe_status fe_tc_apply(fe_mesh* m, const float* X, float* Y, const float* Z, int6
 
 // Y = alpha (Ht - shift) X + beta Z in the requested arithmetic.
 // (plus alpha Ht_nloc X when the mesh carries the nonlocal term)
+// With a Bloch wave vector (Section 2.1, H^k_loc), Ht_k = Ht_0 + |k|^2 / 2 - i A on complex
+// blocks stored as interleaved (re, im) lanes; nvec and ld count real lanes here.  The first
+// launch applies Ht_0 + |k|^2 / 2 to every lane with the Chebyshev combination, the second
+// accumulates alpha (-i A X) into Y (A = M^-1/2 (kx Gx + ky Gy) M^-1/2, real antisymmetric).
 fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t nvec, int64_t ld,
                      double alpha, double beta, double shift, fe_precision prec) {
+  if (m->has_k) {
+    if (prec != FE_F64 && prec != FE_F32)
+      return fe_fail(FE_EUNSUPPORTED, "Bloch operator: FE_F64 and FE_F32 only");
+    if (m->nl.natoms > 0)
+      return fe_fail(FE_EUNSUPPORTED, "Bloch operator: the nonlocal term is Gamma-point only");
+    const double sh = shift - 0.5 * (m->kx * m->kx + m->ky * m->ky);
+    const KronGeom g = fe_geom(m, true);
+    if (prec == FE_F64) {
+      KronIO<double> io{(const double*)X, ld, (double*)Y, ld, (const double*)Z, ld, m->d_veff,
+                        nvec, alpha, beta, sh};
+      FE_TRY(fe::kron_f64(m->coefH, g, io, m->stream));
+      KronIO<double> ia{(const double*)X, ld, (double*)Y, ld, (const double*)Y, ld, nullptr,
+                        nvec, alpha, 1.0, 0.0};
+      return fe::kron_f64(m->coefA, g, ia, m->stream);
+    }
+    KronIO<float> io{(const float*)X, ld, (float*)Y, ld, (const float*)Z, ld, m->d_veff_f, nvec,
+                     (float)alpha, (float)beta, (float)sh};
+    FE_TRY(fe::kron_f32(m->coefH, g, io, m->stream));
+    KronIO<float> ia{(const float*)X, ld, (float*)Y, ld, (const float*)Y, ld, nullptr, nvec,
+                     (float)alpha, 1.0f, 0.0f};
+    return fe::kron_f32(m->coefA, g, ia, m->stream);
+  }
   if (prec == FE_F64) {
     KronIO<double> io{(const double*)X, ld, (double*)Y, ld, (const double*)Z, ld, m->d_veff,
                       nvec, alpha, beta, shift};
@@ -61,6 +87,7 @@ fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t 
 extern "C" fe_status fe_apply_H(fe_mesh* m, const void* X, void* Y, int64_t nvec, int64_t ld,
                                 fe_precision prec) {
   if (!valid_prec(prec)) return fe_fail(FE_EINVAL, "fe_apply_H: bad precision");
+  if (m && m->has_k) { nvec *= 2; ld *= 2; }   // complex entries -> (re, im) lanes
   FE_TRY(check_block(m, X, nvec, ld, elem_bytes(prec), "fe_apply_H"));
   FE_TRY(check_block(m, Y, nvec, ld, elem_bytes(prec), "fe_apply_H"));
   if (!m->has_potential) return fe_fail(FE_EINVAL, "fe_apply_H: call fe_set_potential first");
@@ -74,6 +101,7 @@ extern "C" fe_status fe_apply_H(fe_mesh* m, const void* X, void* Y, int64_t nvec
 extern "C" fe_status fe_cheb_filter(fe_mesh* m, void* X, int64_t nvec, int64_t ld, int degree,
                                     double a, double b, double a0, fe_precision prec) {
   if (!valid_prec(prec)) return fe_fail(FE_EINVAL, "fe_cheb_filter: bad precision");
+  if (m && m->has_k) { nvec *= 2; ld *= 2; }   // complex entries -> (re, im) lanes
   FE_TRY(check_block(m, X, nvec, ld, elem_bytes(prec), "fe_cheb_filter"));
   if (degree < 1) return fe_fail(FE_EINVAL, "fe_cheb_filter: degree must be >= 1");
   if (!(a0 < a && a < b) || !std::isfinite(a0) || !std::isfinite(b))
@@ -142,24 +170,26 @@ __global__ void k_lz_init(const double* __restrict__ v0, double* __restrict__ v,
 }
 
 // f -= s u with the scalar s read on the device
+// (inc 2: the first lane of each node; inc 1: both lanes, the real form of a complex vector)
 __global__ void k_lz_axpy(double* __restrict__ f, const double* __restrict__ u,
-                          const double* __restrict__ s, int64_t n) {
+                          const double* __restrict__ s, int64_t n, int inc) {
   double a = *s;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    f[2 * i] -= a * u[2 * i];
+    f[inc * i] -= a * u[inc * i];
 }
 
 __global__ void k_sqrt(double* x) { *x = sqrt(*x); }
 
 // vold <- v, v <- f / beta
 __global__ void k_lz_shift(const double* __restrict__ f, double* __restrict__ v,
-                           double* __restrict__ vold, const double* __restrict__ beta, int64_t n) {
+                           double* __restrict__ vold, const double* __restrict__ beta, int64_t n,
+                           int inc) {
   double s = 1.0 / *beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    vold[2 * i] = v[2 * i];
-    v[2 * i] = f[2 * i] * s;
+    vold[inc * i] = v[inc * i];
+    v[inc * i] = f[inc * i] * s;
   }
 }
 
@@ -217,15 +247,23 @@ extern "C" fe_status fe_lanczos_bounds(fe_mesh* m, const double* v0, int steps, 
   FE_TRY(fe::dot_async(v0, v0, n, 1, part, tmp, st));
   k_lz_init<<<gb, 256, 0, st>>>(v0, v, f, tmp, n); fe_count_launch();
   FE_CUDA(cudaMemsetAsync(vold, 0, vec_bytes, st));
+  // with a Bloch wave vector the iteration runs on the real form of one complex vector (both
+  // lanes of every node): [[Ht_0 + |k|^2/2, A], [-A, Ht_0 + |k|^2/2]] is symmetric (A is
+  // antisymmetric) and has the spectrum of Ht_k
+  const int lanes = m->has_k ? 2 : 1;
+  const int inc = 2 / lanes;
+  const int64_t nl = n * lanes;
   for (int j = 0; j < steps; ++j) {
     // f = Ht v - beta_{j-1} v_old; alpha_j = f . v; f -= alpha_j v
-    FE_TRY(fe_hx_step(m, v, f, nullptr, 1, 2, 1.0, 0.0, 0.0, FE_F64));
-    if (j) { k_lz_axpy<<<gb, 256, 0, st>>>(f, vold, beta + j - 1, n); fe_count_launch(); }
-    FE_TRY(fe::dot_async(f, v, n, 2, part, alpha + j, st));
-    k_lz_axpy<<<gb, 256, 0, st>>>(f, v, alpha + j, n); fe_count_launch();
-    FE_TRY(fe::dot_async(f, f, n, 2, part, beta + j, st));
+    FE_TRY(fe_hx_step(m, v, f, nullptr, lanes, 2, 1.0, 0.0, 0.0, FE_F64));
+    if (j) { k_lz_axpy<<<gb, 256, 0, st>>>(f, vold, beta + j - 1, nl, inc); fe_count_launch(); }
+    FE_TRY(fe::dot_async(f, v, nl, inc, part, alpha + j, st));
+    k_lz_axpy<<<gb, 256, 0, st>>>(f, v, alpha + j, nl, inc); fe_count_launch();
+    FE_TRY(fe::dot_async(f, f, nl, inc, part, beta + j, st));
     k_sqrt<<<1, 1, 0, st>>>(beta + j); fe_count_launch();
-    if (j + 1 < steps) { k_lz_shift<<<gb, 256, 0, st>>>(f, v, vold, beta + j, n); fe_count_launch(); }
+    if (j + 1 < steps) {
+      k_lz_shift<<<gb, 256, 0, st>>>(f, v, vold, beta + j, nl, inc); fe_count_launch();
+    }
   }
   FE_CUDA(cudaGetLastError());
   std::vector<double> hs(2 * steps);

@@ -13,7 +13,7 @@
 
 #define FE_MAXP 6
 #define FE_MAXN1 (FE_MAXP + 1)
-#define FE_NWS 15   // workspace slots of a mesh
+#define FE_NWS 16   // workspace slots of a mesh
 
 // ---- error state ------------------------------------------------------------------------
 fe_status fe_fail(fe_status st, const char* fmt, ...);
@@ -89,6 +89,8 @@ struct KronCoef {
   double zout;            // 1/2 J^-1/2 (or 1)
   double ax, ay;          // the in-plane stiffness scales hy hz / (2 hx), hx hz / (2 hy)
   int mass_scale;         // 1: Hamiltonian (mass-scaled), 0: plain K
+  int cplx;               // 1: the Bloch first-derivative operator A; the launch writes -i A X
+                          //    on interleaved (re, im) lanes
 };
 
 struct KronGeom {
@@ -165,6 +167,7 @@ struct fe_mesh {
   double h[3], J;
   double xi[FE_MAXN1], w[FE_MAXN1];
   double K1[FE_MAXN1][FE_MAXN1], M1[FE_MAXN1][FE_MAXN1];
+  double G1[FE_MAXN1][FE_MAXN1];   // int l_i l_j' on the reference interval
   cudaStream_t stream;
   int device;
   cudaStream_t aux_stream = nullptr;   // library-owned, non-blocking: graph capture
@@ -172,6 +175,10 @@ struct fe_mesh {
 
   KronCoef coefH;          // Hamiltonian (mass-scaled, 1/2 factor)
   KronCoef coefK;          // plain stiffness
+  // Bloch wave vector (x, y) and the antisymmetric operator M^-1/2 (kx Gx + ky Gy) M^-1/2
+  double kx = 0.0, ky = 0.0;
+  bool has_k = false;
+  KronCoef coefA;
 
   double* d_veff = nullptr;   // [n_psi]
   float* d_veff_f = nullptr;  // [n_psi]
@@ -216,9 +223,12 @@ struct fe_mesh {
 
 enum { WS_CHEB = 0, WS_RR_X = 1, WS_RR_HX = 2, WS_RR_SMALL = 3, WS_CG = 4, WS_RED = 5,
        WS_LANCZOS = 6, WS_TC = 7, WS_TC_IMG = 8, WS_YCELL = 9, WS_RR_TC32 = 10,
-       WS_PCOARSE = 11, WS_NL = 12, WS_KCELL = 13, WS_XC = 14 };
+       WS_PCOARSE = 11, WS_NL = 12, WS_KCELL = 13, WS_XC = 14, WS_KPT = 15 };
 
 fe_status fe_ws(fe_mesh* m, int slot, size_t bytes, void** out);
+// Rayleigh-Ritz of a complex (Bloch) block: nvec, ld count complex entries (fe_kpoint.cu)
+fe_status fe_rr_complex(fe_mesh* m, void* X, int64_t nvec, int64_t ld, double* eig,
+                        fe_precision prec);
 // single-vector float stiffness product through cell-local products (fe_kcell.cu); its
 // scratch (WS_KCELL) is fe_kcell_scratch_bytes
 size_t fe_kcell_scratch_bytes(const fe_mesh* m);

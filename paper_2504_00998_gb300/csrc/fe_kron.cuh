@@ -58,6 +58,7 @@ struct KronCoefT {
   T zout, izout;
   T ax, ay;   // in-plane stiffness scales (used with the compile-time shape tables)
   int mass_scale;
+  int cplx;   // write -i (operator X) on interleaved (re, im) lanes
 };
 
 template <typename T>
@@ -94,6 +95,7 @@ inline KronCoefT<T> convert_coef(const KronCoef& c) {
   o.ax = (T)c.ax;
   o.ay = (T)c.ay;
   o.mass_scale = c.mass_scale;
+  o.cplx = c.cplx;
   return o;
 }
 
@@ -336,8 +338,18 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
       const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
       const T sc = io.alpha * ps * it_sxy[i];
       C out;
+      if (cf.cplx) {
+        // -i (a + i b) = b - i a on each (re, im) lane pair (even chunk widths only)
+        out.zero();
 #pragma unroll
-      for (int e = 0; e < CH; ++e) out.v[e] = sc * acc[i][j].v[e];
+        for (int e = 0; e + 1 < CH; e += 2) {
+          out.v[e] = sc * acc[i][j].v[e + 1];
+          out.v[e + 1] = -sc * acc[i][j].v[e];
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < CH; ++e) out.v[e] = sc * acc[i][j].v[e];
+      }
       if (use_z) {
         const C zc = zsrc[tid + i * NTHR];
 #pragma unroll
@@ -671,8 +683,11 @@ fe_status kron_launch_t(const KronCoef& cf, const KronGeom& g, const KronIO<T>& 
   const bool full = g.NX % TL::BXn == 0 && g.NY % TL::BYn == 0 && io.nvec % vtile == 0;
   auto kern = full ? kron_kernel<T, CH, TL, true, false> : kron_kernel<T, CH, TL, false, false>;
   if constexpr (KronShapeTables<T, CH>::value) {
-    if (cf.mass_scale) kern = full ? kron_kernel<T, CH, TL, true, true> : kron_kernel<T, CH, TL, false, true>;
+    if (cf.mass_scale && !cf.cplx)
+      kern = full ? kron_kernel<T, CH, TL, true, true> : kron_kernel<T, CH, TL, false, true>;
   }
+  if (cf.cplx && (CH % 2 != 0 || io.nvec % 2 != 0))
+    return fe_fail(FE_EINVAL, "complex operator needs interleaved (re, im) lane pairs");
   FE_TRY(kron_func_setup(kern, smem));
   const int64_t nvt = (io.nvec + vtile - 1) / vtile;
   const int64_t total = (int64_t)g.nbx * g.nby * nvt * ((g.nz + g.zseg - 1) / g.zseg);
@@ -778,7 +793,7 @@ fe_status kron_batch_launch_t(const KronCoef& cf, const KronInst<T>* d_inst, int
   if (total < 1 || total > 0x7fffffffLL) return fe_fail(FE_EINVAL, "batched grid of %lld CTAs", (long long)total);
   auto kern = full ? kron_batch_kernel<T, CH, TL, true, false> : kron_batch_kernel<T, CH, TL, false, false>;
   if constexpr (KronShapeTables<T, CH>::value) {
-    if (cf.mass_scale)
+    if (cf.mass_scale && !cf.cplx)
       kern = full ? kron_batch_kernel<T, CH, TL, true, true> : kron_batch_kernel<T, CH, TL, false, true>;
   }
   FE_TRY(kron_func_setup(kern, smem));

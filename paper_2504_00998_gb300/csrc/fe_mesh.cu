@@ -107,7 +107,7 @@ static void element_matrices(fe_mesh* m) {
   double gq[FE_MAXN1 + 1], gw[FE_MAXN1 + 1];
   gauss_rule(n1, gq, gw);
   for (int i = 0; i < n1; ++i)
-    for (int j = 0; j < n1; ++j) { m->K1[i][j] = 0.0; m->M1[i][j] = 0.0; }
+    for (int j = 0; j < n1; ++j) { m->K1[i][j] = 0.0; m->M1[i][j] = 0.0; m->G1[i][j] = 0.0; }
   for (int a = 0; a < n1; ++a) {
     double l[FE_MAXN1], dl[FE_MAXN1];
     for (int i = 0; i < n1; ++i) lagrange(n1, m->xi, i, gq[a], &l[i], &dl[i]);
@@ -115,6 +115,7 @@ static void element_matrices(fe_mesh* m) {
       for (int j = 0; j < n1; ++j) {
         m->K1[i][j] += gw[a] * dl[i] * dl[j];
         m->M1[i][j] += gw[a] * l[i] * l[j];
+        m->G1[i][j] += gw[a] * l[i] * dl[j];
       }
   }
 }
@@ -145,6 +146,26 @@ static void build_coef(fe_mesh* m, bool hamiltonian, KronCoef* c) {
   c->mass_scale = hamiltonian ? 1 : 0;
   c->zin = hamiltonian ? 1.0 / std::sqrt(m->J) : 1.0;
   c->zout = hamiltonian ? 0.5 / std::sqrt(m->J) : 1.0;
+}
+
+// The Bloch operator A = M^-1/2 (kx Gx + ky Gy) M^-1/2 (Section 2.1, the -i k.grad term of
+// H^k_loc) in the tensor-product form of KronCoef: G^x = (hy hz / 4) G1 (x) M1 (x) M1 over
+// the reference matrices (x derivative; y and z masses), G^y likewise; no z derivative, so
+// AzK = 0; the symmetric mass scaling of the Hamiltonian without its factor 1/2.
+static void build_coef_bloch(fe_mesh* m, KronCoef* c) {
+  build_coef(m, true, c);
+  const int n1 = m->p + 1;
+  const double hx = m->h[0], hy = m->h[1], hz = m->h[2];
+  const double gx = m->kx * hy * hz / 4.0, gy = m->ky * hx * hz / 4.0;
+  for (int j = 0; j < n1; ++j)
+    for (int k = 0; k < n1; ++k) {
+      c->AxK[j][k] = gx * m->G1[j][k] * c->sig[k];
+      c->AyK[j][k] = gy * m->G1[j][k] * c->sig[k];
+      c->AzK[j][k] = 0.0;
+    }
+  c->zout = 1.0 / std::sqrt(m->J);
+  c->ax = c->ay = 0.0;
+  c->cplx = 1;
 }
 
 // ---- device helpers -------------------------------------------------------------------------
@@ -434,4 +455,15 @@ KronGeom fe_geom(const fe_mesh* m, bool psi) {
   g.NZs = psi ? m->NZs : m->NZ;
   g.bx = g.by = g.zseg = g.nbx = g.nby = 0;   // chosen by the launcher
   return g;
+}
+
+extern "C" fe_status fe_set_kpoint(fe_mesh* m, double kx, double ky) {
+  if (!m) return fe_fail(FE_EINVAL, "fe_set_kpoint: null mesh");
+  if (!std::isfinite(kx) || !std::isfinite(ky))
+    return fe_fail(FE_EINVAL, "fe_set_kpoint: k must be finite");
+  m->kx = kx;
+  m->ky = ky;
+  m->has_k = kx != 0.0 || ky != 0.0;
+  if (m->has_k) build_coef_bloch(m, &m->coefA);
+  return FE_OK;
 }

@@ -343,6 +343,15 @@ extern "C" fe_status fe_rayleigh_ritz(fe_mesh* m, void* X, int64_t nvec, int64_t
   if (nvec > m->n_psi) return fe_fail(FE_EINVAL, "fe_rayleigh_ritz: nvec exceeds the node count");
   if (prec != FE_F64 && prec != FE_F32 && prec != FE_BF16_F32ACC && prec != FE_F32_F32ACC)
     return fe_fail(FE_EINVAL, "fe_rayleigh_ritz: bad precision");
+  if (m->has_k) {
+    // complex block (interleaved re, im; nvec and ld count complex entries)
+    const int ceb = prec == FE_F64 ? 16 : 8;
+    if (((uintptr_t)X) % 16 || (ld * ceb) % 16)
+      return fe_fail(FE_EINVAL, "fe_rayleigh_ritz: block alignment");
+    if (!m->has_potential) return fe_fail(FE_EINVAL, "fe_rayleigh_ritz: call fe_set_potential first");
+    FE_TRY(fe_activate(m));
+    return fe_rr_complex(m, X, nvec, ld, eig, prec);
+  }
   const int eb = prec == FE_F64 ? 8 : 4;
   if (((uintptr_t)X) % 16 || (ld * eb) % 16)
     return fe_fail(FE_EINVAL, "fe_rayleigh_ritz: block alignment");

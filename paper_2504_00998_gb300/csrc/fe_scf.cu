@@ -35,12 +35,13 @@ __global__ void k_lda_exchange(const double* __restrict__ rho, double* __restric
 }
 
 // one warp per psi node: lanes stride over the vectors
+// (cshift 1: complex orbitals as interleaved (re, im) lanes, lanes 2n and 2n+1 share occ_n)
 template <typename T>
 __global__ void k_density(const T* __restrict__ X, int64_t ld, int64_t nvec,
                           const double* __restrict__ occ, const double* __restrict__ mass,
-                          int64_t off, int64_t npsi, double* __restrict__ rho) {
+                          int64_t off, int64_t npsi, double* __restrict__ rho, int cshift) {
   extern __shared__ double s_occ[];
-  for (int64_t v = threadIdx.x; v < nvec; v += blockDim.x) s_occ[v] = occ[v];
+  for (int64_t v = threadIdx.x; v < nvec; v += blockDim.x) s_occ[v] = occ[v >> cshift];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -186,6 +187,9 @@ extern "C" fe_status fe_density(fe_mesh* m, const void* X, int64_t nvec, int64_t
     return fe_fail(FE_EUNSUPPORTED, "fe_density: FE_F64 and FE_F32 blocks only");
   if (nvec < 1 || ld < nvec || nvec > 4096)
     return fe_fail(FE_EINVAL, "fe_density: need 1 <= nvec <= ld, nvec <= 4096");
+  const int cshift = m->has_k ? 1 : 0;   // complex orbitals: |u|^2 = re^2 + im^2
+  nvec <<= cshift;
+  ld <<= cshift;
   FE_TRY(fe_activate(m));
   cudaStream_t st = m->stream;
   const int64_t plane = (int64_t)m->NX * m->NY;
@@ -200,10 +204,10 @@ extern "C" fe_status fe_density(fe_mesh* m, const void* X, int64_t nvec, int64_t
   const size_t smem = sizeof(double) * (size_t)nvec;
   if (prec == FE_F64)
     k_density<double><<<(int)blocks, threads, smem, st>>>((const double*)X, ld, nvec, occ, m->d_mass,
-                                                          off, m->n_psi, rho);
+                                                          off, m->n_psi, rho, cshift);
   else
     k_density<float><<<(int)blocks, threads, smem, st>>>((const float*)X, ld, nvec, occ, m->d_mass,
-                                                         off, m->n_psi, rho);
+                                                         off, m->n_psi, rho, cshift);
   fe_count_launch();
   FE_CUDA(cudaGetLastError());
   return FE_OK;

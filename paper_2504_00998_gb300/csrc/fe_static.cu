@@ -53,6 +53,8 @@ extern "C" fe_status fe_cheb_filter_static(fe_mesh* m, void* X, int64_t nvec, in
                                            int degree, double a, double b, double a0,
                                            fe_precision prec) {
   if (!m || !X) return fe_fail(FE_EINVAL, "fe_cheb_filter_static: null argument");
+  if (m->has_k)
+    return fe_fail(FE_EUNSUPPORTED, "fe_cheb_filter_static: Gamma-point blocks only");
   if (prec != FE_F64 && prec != FE_F32)
     return fe_fail(FE_EUNSUPPORTED,
                    "fe_cheb_filter_static: only FE_F64 and FE_F32 run without allocation");

@@ -87,3 +87,31 @@ def test_band_state_has_the_plane_wave_phase():
     x = om.phi_coords()[ids][:, 0]
     w = u * np.exp(-1j * g * x)          # constant for the e^{+i g x} state
     assert np.max(np.abs(w - w.mean())) <= 1e-3 * np.max(np.abs(w))
+
+
+def test_complex_filter_is_the_polynomial_of_the_spectrum():
+    """The oracle's filter on a complex block equals V p(Lambda) V^H X from the dense
+    eigendecomposition of Ht_k (p the scaled Chebyshev polynomial evaluated by its own
+    three-term recurrence on the eigenvalues)."""
+    from oracle import chefsi
+    om = _mesh(p=2, ncell=(2, 2, 2))
+    rng = np.random.default_rng(3)
+    V = rng.uniform(-1.0, 0.5, om.n_psi)
+    Hk = kpoint.hamiltonian_k(om, V, (0.3, -0.2)).toarray()
+    lam, Q = sla.eigh(Hk)
+    X = rng.standard_normal((om.n_psi, 3)) + 1j * rng.standard_normal((om.n_psi, 3))
+    a0, b = lam[0] - 0.1, lam[-1] + 0.1
+    a = a0 + 0.3 * (b - a0)
+    deg = 6
+    got = chefsi.cheb_filter(lambda Z: Hk @ Z, X, deg, a, b, a0)
+    # the same recurrence on the scalars lambda
+    e, c = (b - a) / 2, (b + a) / 2
+    sig = e / (a0 - c)
+    tau = 2 / sig
+    y0, y1 = np.ones_like(lam), (sig / e) * (lam - c)
+    for _ in range(2, deg + 1):
+        sn = 1 / (tau - sig)
+        y0, y1 = y1, (2 * sn / e) * (lam - c) * y1 - sig * sn * y0
+        sig = sn
+    ref = Q @ (y1[:, None] * (Q.conj().T @ X))
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
