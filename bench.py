@@ -42,12 +42,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--prec", choices=["f32", "f64", "bf16"], default="f32")
-    ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep", "p5nl", "scf"],
+    ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep", "p5nl", "scf", "p5k"],
                     default="p5",
                     help="p5: the benchmark slab; p5s / p3: smaller slabs; sweep: the batched "
                          "bias sweep of 24 independent 8x8xH-cell p=4 slabs; p5nl: the "
                          "benchmark step with synthetic nonlocal projectors on every atom; "
-                         "scf: self-consistent iterations on the benchmark slab")
+                         "scf: self-consistent iterations on the benchmark slab; p5k: the "
+                         "benchmark step at a Bloch wave vector (complex block of the same size)")
     ap.add_argument("--rr", choices=["f64", "tc32"], default="tc32",
                     help="Rayleigh-Ritz block products for float storage: double GEMMs or "
                          "FP32-accurate tensor-core emulation (n x n part always double)")
@@ -59,7 +60,7 @@ def parse():
 def workload(name):
     """p5: the benchmark slab; p5s: the same p = 5 cells and vectors with 16 cell layers and
     256 vectors (a 0.5 GB block, above L2) for profiler captures; p3: the small CEF slab."""
-    if name in ("p5", "p5nl", "scf"):
+    if name in ("p5", "p5nl", "scf", "p5k"):
         return W.config2()
     if name == "p5s":
         s = W.config2()
@@ -307,6 +308,11 @@ def run_gpu(args):
     if prec != fe.FE_F64:
         m.set_rr_products(args.rr == "tc32")
     nl_desc = ""
+    if args.workload == "p5k":
+        # Bloch wave vector k = (0.1, 0.05) / bohr: the block is complex (the same bytes as
+        # the Gamma-point block: nvec / 2 complex vectors)
+        m.set_kpoint(0.1, 0.05)
+        nl_desc = f" at k = (0.1, 0.05) / bohr with {slab.nvec // 2} complex vectors"
     if args.workload == "p5nl":
         # synthetic s + p projectors on every atom (the stand-in for the pseudopotentials'
         # nonlocal part): width 0.8 bohr, cut at 2.6 bohr, D = (1.0, 0.4, 0.4, 0.4) Ha
@@ -323,6 +329,8 @@ def run_gpu(args):
 
     X0 = torch.from_numpy(W.start_block(slab)).pin_memory()
     X = torch.empty((m.n_psi, nvec), dtype=fe.storage_dtype(prec), device=dev)
+    # the block the step works on: X itself, or its complex view at a Bloch wave vector
+    blk = torch.view_as_complex(X.view(m.n_psi, nvec // 2, 2)) if args.workload == "p5k" else X
     X.copy_(X0.to(X.dtype) if X.dtype != X0.dtype else X0)
     st = torch.cuda.current_stream(dev)
 
@@ -342,10 +350,10 @@ def run_gpu(args):
         m.set_potential(vb)
         if rec:
             e[2].record(st)
-        m.cheb_filter(X, degree, a, b, a0, prec=prec)
+        m.cheb_filter(blk, degree, a, b, a0, prec=prec)
         if rec:
             e[3].record(st)
-        eig = m.rayleigh_ritz(X, prec=prec)
+        eig = m.rayleigh_ritz(blk, prec=prec)
         if rec:
             e[4].record(st)
             marks.append(e)
@@ -401,7 +409,7 @@ def run_gpu(args):
     # stream while the Poisson solve runs (the solve does not read the block), and the
     # filter waits for it.
     Xh = X.cpu().pin_memory()
-    eig_h = torch.empty(nvec, dtype=torch.float64).pin_memory()
+    eig_h = torch.empty(blk.shape[1], dtype=torch.float64).pin_memory()
     cs = torch.cuda.Stream(dev)
 
     def step_e2e():
@@ -413,8 +421,8 @@ def run_gpu(args):
         m.poisson_solve(slab.bias, rtol=POISSON_RTOL, phi=phi, vbare=vb)
         m.set_potential(vb)
         st.wait_event(arrived)
-        m.cheb_filter(X, degree, a, b, a0, prec=prec)
-        return m.rayleigh_ritz(X, prec=prec)
+        m.cheb_filter(blk, degree, a, b, a0, prec=prec)
+        return m.rayleigh_ritz(blk, prec=prec)
 
     torch.cuda.synchronize(dev)
     e2e_start, e2e_end = ev(), ev()
@@ -430,7 +438,8 @@ def run_gpu(args):
     e2e_val = aggregate_value(world, flops_step, e2e_ms)
 
     extra = {}
-    if rank == 0 and world == 1 and not args.no_fp64_compare and prec != fe.FE_F64:
+    if (rank == 0 and world == 1 and not args.no_fp64_compare and prec != fe.FE_F64
+            and args.workload != "p5k"):
         # one cycle of both paths from the same start block: Ritz-value difference and the
         # FP64 filter's throughput
         # two cycles (the second starts from an orthonormal block, as in an SCF loop)
@@ -460,7 +469,7 @@ def run_gpu(args):
         torch.cuda.empty_cache()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "p5k":
         cpu = cpu_baseline_oracle(slab, nvec)
         cpu.pop("seconds", None)
 
