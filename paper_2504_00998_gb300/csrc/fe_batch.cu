@@ -475,7 +475,8 @@ extern "C" fe_status fe_batch_rayleigh_ritz(fe_batch* b, void* const* X, int64_t
       rmax = std::fmax(rmax, std::fabs(hrd[(size_t)i * n + j]));
       rmin = std::fmin(rmin, std::fabs(hrd[(size_t)i * n + j]));
     }
-    ill[i] = hinfo[i] != 0 || !(rmin > 0.0) || (rmax / rmin) * (rmax / rmin) > 1e8;
+    ill[i] = hinfo[i] != 0 || !(rmin > 0.0) ||
+             (rmax / rmin) * (rmax / rmin) > (prec == FE_F32 ? kGramCondTC32 : kGramCondF64);
   }
   const double one = 1.0;
   // G = R^-T H R^-1

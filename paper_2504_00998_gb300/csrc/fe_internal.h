@@ -69,6 +69,14 @@ struct FiniteEmulationGuard {
   FiniteEmulationGuard& operator=(const FiniteEmulationGuard&) = delete;
 };
 
+// ---- Gram-path acceptance -------------------------------------------------------------------
+// Largest cond(D S D) (D S D the diagonally scaled Gram matrix) for which the Rayleigh-Ritz
+// Gram path is used: its results degrade like cond times the relative error of the Gram
+// products, so double products (about 1e-16) allow 1e8 and FP32-accurate tensor-core ones
+// (about 1e-7) 1e4.  Above it the block takes the explicit or double path.
+constexpr double kGramCondF64 = 1e8;
+constexpr double kGramCondTC32 = 1e4;
+
 // ---- tensor-product operator arguments ----------------------------------------------------
 // The assembled stiffness of the tensor-product mesh is
 //   K = ax K1 (x) M1 (x) M1 + ay M1 (x) K1 (x) M1 + az M1 (x) M1 (x) K1   (x (x) y (x) z),

@@ -338,7 +338,8 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
       const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
       const T sc = io.alpha * ps * it_sxy[i];
       C out;
-      if (cf.cplx) {
+      // (the shape-table variants are launched for the real operator only)
+      if (!CT && cf.cplx) {
         // -i (a + i b) = b - i a on each (re, im) lane pair (even chunk widths only)
         out.zero();
 #pragma unroll

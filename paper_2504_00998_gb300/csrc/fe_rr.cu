@@ -11,8 +11,8 @@
 // X C is the Rayleigh-Ritz basis of span(X) with C^T S C = I: the same result as
 // Cholesky-QR followed by Rayleigh-Ritz, with the orthonormalisation folded into the n x n
 // problem.  Its orthogonality degrades like cond(D S D) u, so when the Cholesky fails or
-// the factor's diagonal indicates cond(D S D) > 1e8 (cold starts from random blocks) the
-// explicit path runs instead:
+// the factor's diagonal indicates cond(D S D) > 1e8 (1e4 with FP32-accurate products; cold
+// starts from random blocks) the explicit path runs instead:
 //   scaled Cholesky-QR2, or shifted Cholesky-QR3 when the first factorisation breaks down
 //   (shift 11 (N n + n (n+1)) u n; Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa, SIAM
 //   J. Sci. Comput. 2020), then Hs = X^T (Ht X), eigh, X <- X Q.
@@ -164,8 +164,8 @@ __global__ void k_diag(const double* __restrict__ R, int n, double* __restrict__
 
 // n x n part of the Gram path.  On entry w.S holds X^T X (upper triangle at least) and w.Q
 // holds X^T Ht X; on exit w.Q holds C = D R^-1 Q and eig the Ritz values, or *ill is set
-// when the scaled Gram matrix is not safely positive definite.
-fe_status rr_small(fe_mesh* m, int64_t nvec, RrWs& w, double* eig, bool* ill) {
+// when the scaled Gram matrix is not safely positive definite (cond above cond_max).
+fe_status rr_small(fe_mesh* m, int64_t nvec, RrWs& w, double* eig, bool* ill, double cond_max) {
   const int n = (int)nvec;
   cudaStream_t st = m->stream;
   const double one = 1.0;
@@ -189,7 +189,7 @@ fe_status rr_small(fe_mesh* m, int64_t nvec, RrWs& w, double* eig, bool* ill) {
     rmax = std::fmax(rmax, std::fabs(rdiag[j]));
     rmin = std::fmin(rmin, std::fabs(rdiag[j]));
   }
-  if (!(rmin > 0.0) || (rmax / rmin) * (rmax / rmin) > 1e8) { *ill = true; return FE_OK; }
+  if (!(rmin > 0.0) || (rmax / rmin) * (rmax / rmin) > cond_max) { *ill = true; return FE_OK; }
   // G = R^-T Hs R^-1
   FE_CUBLAS(cublasDtrsm(m->cublas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_T,
                         CUBLAS_DIAG_NON_UNIT, n, n, &one, w.S, n, w.Q, n));
@@ -218,7 +218,7 @@ fe_status rr_gram_path(fe_mesh* m, const double* X, int64_t ld, const double* HX
   FE_CUBLAS(cublasDsyrk(m->cublas, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N, n, (int)m->n_psi, &one,
                         X, (int)ld, &zero, w.S, n));
   FE_TRY(gram(m, X, ld, HX, ldh, nvec, w.Q));
-  FE_TRY(rr_small(m, nvec, w, eig, ill));
+  FE_TRY(rr_small(m, nvec, w, eig, ill, kGramCondF64));
   if (*ill) return FE_OK;
   // Xout^T = C^T A
   FE_CUBLAS(cublasDgemm(m->cublas, CUBLAS_OP_T, CUBLAS_OP_N, n, (int)m->n_psi, n, &one, w.Q, n,
@@ -259,7 +259,7 @@ fe_status rr_gram_path_tc32(fe_mesh* m, float* X, int64_t ld, const float* HX, i
   const int64_t nn = (int64_t)n * n;
   k_f2d_n<<<fe::grid_for(nn), 256, 0, m->stream>>>(Sf, w.S, nn); fe_count_launch();
   k_f2d_n<<<fe::grid_for(nn), 256, 0, m->stream>>>(Hf, w.Q, nn); fe_count_launch();
-  FE_TRY(rr_small(m, nvec, w, eig, ill));
+  FE_TRY(rr_small(m, nvec, w, eig, ill, kGramCondTC32));
   if (*ill) return FE_OK;
   k_d2f_n<<<fe::grid_for(nn), 256, 0, m->stream>>>(w.Q, Sf, nn); fe_count_launch();
   // tmp^T = C^T A

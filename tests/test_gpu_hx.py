@@ -173,3 +173,20 @@ def test_rayleigh_ritz_tensor_core_products(fe):
     assert np.max(np.abs(lam - lam_ref)) <= 1e-4
     Q = Xg.double().cpu().numpy()
     assert np.max(np.abs(Q.T @ Q - np.eye(12))) <= 1e-5
+
+
+def test_rayleigh_ritz_tensor_core_products_decline_an_ill_conditioned_block(fe):
+    """Nearly dependent columns (cond of the scaled Gram matrix ~1e10, beyond what FP32-accurate
+    products resolve): the tensor-core Gram path declines and the double path gives the Ritz
+    values of the float block's span."""
+    om, H, m, rng = _setup(fe, (4.0, 4.0, 9.0), (2, 2, 4), 3, (True, True), seed=15)
+    m.set_rr_products(True)
+    B = rng.standard_normal((om.n_psi, 8))
+    B[:, 7] = B[:, 6] + 1e-5 * (B[:, 5] + B[:, 7])
+    X = B.astype(np.float32).astype(np.float64)
+    lam_ref, _ = chefsi.rayleigh_ritz(lambda Z: H @ Z, X)
+    Xg = torch.tensor(X, dtype=torch.float32, device="cuda")
+    lam = m.rayleigh_ritz(Xg, prec=fe.FE_F32).cpu().numpy()
+    assert np.max(np.abs(lam - lam_ref)) <= 1e-5 * max(1.0, np.max(np.abs(lam_ref)))
+    Q = Xg.double().cpu().numpy()
+    assert np.max(np.abs(Q.T @ Q - np.eye(8))) <= 1e-5

@@ -95,17 +95,23 @@ def test_complex_filter_matches_oracle(fe, prec, tol):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_complex_rayleigh_ritz(fe, prec):
+@pytest.mark.parametrize("prec,tc", [("f64", False), ("f32", False), ("f32", True)])
+@pytest.mark.parametrize("nvec", [1, 10, 33])
+def test_complex_rayleigh_ritz(fe, prec, tc, nvec):
     """Ritz values against the oracle's (orthonormal basis by QR, eigvalsh of Q^H Ht_k Q);
-    the rotated block is orthonormal and its Rayleigh quotients are the Ritz values."""
+    the rotated block is orthonormal and its Rayleigh quotients are the Ritz values.  tc: the
+    float block's products as real tensor-core GEMMs on its (re, im) lanes."""
     L, ncell, p, faces, k = CASES[0]
     om, Hk, m, rng, V = _setup(fe, L, ncell, p, faces, k)
-    nvec = 10
+    m.set_rr_products(tc)
     X = _cblock(rng, om.n_psi, nvec)
     P = fe.FE_F64 if prec == "f64" else fe.FE_F32
     dt = torch.complex128 if prec == "f64" else torch.complex64
-    Xg = torch.tensor(X, dtype=dt, device="cuda")
+    # rows are 16-byte multiples: complex64 blocks take an even leading dimension
+    ld = nvec + (nvec % 2 if prec == "f32" else 0)
+    buf = torch.zeros((om.n_psi, ld), dtype=dt, device="cuda")
+    buf[:, :nvec] = torch.tensor(X, dtype=dt)
+    Xg = buf[:, :nvec]
     Xin = Xg.cpu().numpy().astype(np.complex128)
     e = m.rayleigh_ritz(Xg, prec=P).cpu().numpy()
     Q, _ = np.linalg.qr(Xin)
@@ -119,19 +125,44 @@ def test_complex_rayleigh_ritz(fe, prec):
     assert np.max(np.abs(rq - e)) <= (1e-9 if prec == "f64" else 1e-4) * scale
 
 
-def test_subspace_iteration_converges_to_the_dense_spectrum(fe):
+@pytest.mark.parametrize("prec,tc,tol", [("f64", False, 1e-8), ("f32", True, 2e-5)])
+def test_subspace_iteration_converges_to_the_dense_spectrum(fe, prec, tc, tol):
     L, ncell, p, faces, k = CASES[1]
     om, Hk, m, rng, V = _setup(fe, L, ncell, p, faces, k)
+    m.set_rr_products(tc)
     ev = sla.eigvalsh(Hk.toarray())
     nvec, want = 12, 6
-    X = torch.tensor(_cblock(rng, om.n_psi, nvec), device="cuda")
+    P = fe.FE_F64 if prec == "f64" else fe.FE_F32
+    dt = torch.complex128 if prec == "f64" else torch.complex64
+    X = torch.tensor(_cblock(rng, om.n_psi, nvec), dtype=dt, device="cuda")
     lo, hi = m.lanczos_bounds(torch.ones(om.n_psi, dtype=torch.float64, device="cuda"), 30)
     cut = lo + 0.1 * (hi - lo)
     for _ in range(25):
-        m.cheb_filter(X, 10, cut, hi, lo, prec=fe.FE_F64)
-        e = m.rayleigh_ritz(X, prec=fe.FE_F64).cpu().numpy()
+        m.cheb_filter(X, 10, cut, hi, lo, prec=P)
+        e = m.rayleigh_ritz(X, prec=P).cpu().numpy()
         cut = float(e[-1])
-    assert np.max(np.abs(e[:want] - ev[:want])) <= 1e-8 * max(1.0, abs(ev[want - 1]))
+    assert np.max(np.abs(e[:want] - ev[:want])) <= tol * max(1.0, abs(ev[want - 1]))
+
+
+def test_tc_rayleigh_ritz_falls_back_on_an_ill_conditioned_block(fe):
+    """Columns that are nearly dependent (cond of the scaled Gram matrix far above 1e8): the
+    tensor-core Gram path declines and the double complex path gives the Ritz values of the
+    span."""
+    L, ncell, p, faces, k = CASES[0]
+    om, Hk, m, rng, V = _setup(fe, L, ncell, p, faces, k)
+    m.set_rr_products(True)
+    nvec = 6
+    B = _cblock(rng, om.n_psi, nvec)
+    B[:, 5] = B[:, 4] + 1e-5 * ((1.0 + 0.5j) * B[:, 3] + B[:, 5])
+    Xg = torch.tensor(B, dtype=torch.complex64, device="cuda")
+    Xin = Xg.cpu().numpy().astype(np.complex128)
+    e = m.rayleigh_ritz(Xg, prec=fe.FE_F32).cpu().numpy()
+    Q, _ = np.linalg.qr(Xin)
+    ref = sla.eigvalsh(Q.conj().T @ (Hk @ Q))
+    scale = max(1.0, np.max(np.abs(ref)))
+    assert np.max(np.abs(e - ref)) <= 1e-5 * scale
+    Xr = Xg.cpu().numpy().astype(np.complex128)
+    assert np.max(np.abs(Xr.conj().T @ Xr - np.eye(nvec))) <= 1e-5
 
 
 def test_free_electron_ground_state_on_gpu(fe):
