@@ -25,6 +25,12 @@ ab initio modeling of surfaces and interfaces under external potential bias"):
                    (Section 2.3 points to prior work for the eigensolver; the scaled
                    three-term filter of Zhou & Saad, J. Comput. Phys. 2006, Lanczos
                    bounds of Zhou & Li 2011, Householder QR + dense eigh).
+* kpoint.py     -- the Bloch k-point Hamiltonian (Section 2.1, Bloch's theorem in x, y).
+* quadpot.py    -- the potential term integrated by Gauss quadrature (the consistent
+                   cell-matrix form of V in Section 2.3), V given at Gauss points.
+* analysis.py, projectors.py, scf.py -- analysis outputs, synthetic nonlocal projectors
+                   and the self-consistent closure (their module headers cite the
+                   passages).
 
 Parity status: every function above is pinned by tests/test_oracle_*.py against
 closed forms, patch tests, brute force or textbook identities, except the readings
