@@ -42,13 +42,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--prec", choices=["f32", "f64", "bf16"], default="f32")
-    ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep", "p5nl", "scf", "p5k"],
+    ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep", "p5nl", "scf", "p5k",
+                                           "p5q"],
                     default="p5",
                     help="p5: the benchmark slab; p5s / p3: smaller slabs; sweep: the batched "
                          "bias sweep of 24 independent 8x8xH-cell p=4 slabs; p5nl: the "
                          "benchmark step with synthetic nonlocal projectors on every atom; "
                          "scf: self-consistent iterations on the benchmark slab; p5k: the "
-                         "benchmark step at a Bloch wave vector (complex block of the same size)")
+                         "benchmark step at a Bloch wave vector (complex block of the same "
+                         "size); p5q: the benchmark step with the potential integrated by "
+                         "Gauss quadrature (V_bare interpolated to the Gauss points)")
     ap.add_argument("--rr", choices=["f64", "tc32"], default="tc32",
                     help="Rayleigh-Ritz block products for float storage: double GEMMs or "
                          "FP32-accurate tensor-core emulation (n x n part always double)")
@@ -60,7 +63,7 @@ def parse():
 def workload(name):
     """p5: the benchmark slab; p5s: the same p = 5 cells and vectors with 16 cell layers and
     256 vectors (a 0.5 GB block, above L2) for profiler captures; p3: the small CEF slab."""
-    if name in ("p5", "p5nl", "scf", "p5k"):
+    if name in ("p5", "p5nl", "scf", "p5k", "p5q"):
         return W.config2()
     if name == "p5s":
         s = W.config2()
@@ -319,10 +322,21 @@ def run_gpu(args):
         na = len(slab.R)
         m.set_nonlocal(slab.R, np.full(na, 0.8), np.tile([1.0, 0.4, 0.4, 0.4], (na, 1)), 2.6)
         nl_desc = f" + synthetic s,p nonlocal projectors on all {na} atoms (sigma 0.8, cut 2.6 bohr)"
+    if args.workload == "p5q":
+        nl_desc = (f" with the potential integrated by {slab.p + 1}^3-point Gauss quadrature "
+                   "(V_bare interpolated to the Gauss points)")
     phi = torch.empty(m.n_phi, dtype=torch.float64, device=dev)
     vb = torch.empty(m.n_psi, dtype=torch.float64, device=dev)
+
+    def set_pot():
+        # V_eff at the psi nodes (collocated), or at every cell's Gauss points
+        if args.workload == "p5q":
+            m.set_potential_quad(m.interp_quad(m.vbare_phi(phi, slab.bias)))
+        else:
+            m.set_potential(vb)
+
     m.poisson_solve(slab.bias, rtol=POISSON_RTOL, phi=phi, vbare=vb)
-    m.set_potential(vb)
+    set_pot()
     lo, hi = m.lanczos_bounds(torch.tensor(W.lanczos_start(m.n_psi), device=dev), LANCZOS_STEPS)
     a0, b = lo, hi
     a = a0 + R_FILTER * (b - a0)
@@ -347,7 +361,7 @@ def run_gpu(args):
         pinfo["iters"], pinfo["rel_residual"] = info.iters, info.rel_residual
         if rec:
             e[1].record(st)
-        m.set_potential(vb)
+        set_pot()
         if rec:
             e[2].record(st)
         m.cheb_filter(blk, degree, a, b, a0, prec=prec)
@@ -419,7 +433,7 @@ def run_gpu(args):
             X.copy_(Xh, non_blocking=True)
             arrived.record(cs)
         m.poisson_solve(slab.bias, rtol=POISSON_RTOL, phi=phi, vbare=vb)
-        m.set_potential(vb)
+        set_pot()
         st.wait_event(arrived)
         m.cheb_filter(blk, degree, a, b, a0, prec=prec)
         return m.rayleigh_ritz(blk, prec=prec)
@@ -469,7 +483,8 @@ def run_gpu(args):
         torch.cuda.empty_cache()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "p5k":
+    if (rank == 0 and world == 1 and not args.no_cpu_baseline
+            and args.workload not in ("p5k", "p5q")):
         cpu = cpu_baseline_oracle(slab, nvec)
         cpu.pop("seconds", None)
 

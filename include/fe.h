@@ -161,6 +161,25 @@ fe_status fe_set_kpoint(fe_mesh* mesh, double kx, double ky);
  * V_eff = phi + V_loc - V_sm + V_app).  Copied into the mesh. */
 fe_status fe_set_potential(fe_mesh* mesh, const double* veff_dev);
 
+/* Potential term integrated by Gauss quadrature instead of GLL collocation: the consistent
+ * FE matrix V_IJ = int N_I V_eff N_J dx of the discretised Kohn-Sham operator (Section 2.3),
+ * evaluated cell by cell with the (p+1)-point Gauss-Legendre rule per direction from V_eff
+ * at the Gauss points: vq_dev[n_cells][(p+1)^3] (device, double), cells with cx fastest then
+ * cy then cz, point (a, b, c) (a along x) at a + (p+1)(b + (p+1) c), Gauss points ascending
+ * on each cell's interval.  The operator becomes Ht = M^-1/2 (1/2 K + V) M^-1/2 with the
+ * lumped overlap M; the cell matrices are applied in sum-factorised form, never stored.
+ * Values are copied into the mesh (weights w |J| V folded in).  Replaces the collocated
+ * potential for fe_apply_H, fe_cheb_filter(_static), fe_lanczos_bounds and
+ * fe_rayleigh_ritz (any precision; complex blocks too) until fe_set_potential is called
+ * again; fe_batch_create and the batched entry points refuse such a mesh (FE_EUNSUPPORTED).
+ * FE_EINVAL for null arguments, FE_ENOMEM when its tables cannot be allocated. */
+fe_status fe_set_potential_quad(fe_mesh* mesh, const double* vq_dev);
+
+/* Values at every cell's Gauss points (layout of fe_set_potential_quad) of the FE field
+ * with nodal values f_phi_dev[n_phi] (device, double): f(x_q) = sum_I N_I(x_q) f_I
+ * (Section 2.3 basis).  out_dev[n_cells][(p+1)^3] (device, double, caller-owned). */
+fe_status fe_interp_quad(fe_mesh* mesh, const double* f_phi_dev, double* out_dev);
+
 /* Y = Ht X (Eq. Veff and Hloc, Section 2.3).  X, Y [n_psi][ld], nvec vectors; X and Y
  * must not overlap.  Needs fe_set_potential first. */
 fe_status fe_apply_H(fe_mesh* mesh, const void* X, void* Y, int64_t nvec, int64_t ld,

@@ -93,25 +93,27 @@ def apply_Hq_rows(mesh, Vq, X, rows, M=None):
     """(Ht_q X)[rows, :] from the cell definition, one row at a time (for sizes where the
     assembled matrix does not fit): the stiffness part as in assembly.apply_H_rows with a
     zero collocated potential, plus S_I sum over the cells e touching I of
-    sum_J V_e[l_I, J] (S X)_{node_e(J)} (S = M^-1/2, X = 0 on Dirichlet nodes)."""
+    sum_J V_e[l_I, J] (S X)_{node_e(J)} (S = M^-1/2, X = 0 on Dirichlet nodes).  X may be
+    float32; only the rows the sampled cells touch are promoted."""
     M = assembly.lumped_mass(mesh) if M is None else M
-    X = np.asarray(X, dtype=np.float64)
+    X = np.asarray(X)
     out = assembly.apply_H_rows(mesh, np.zeros(mesh.n_psi), X, rows, M=M)
     B, W = reference_interpolation(mesh)
     Vq = np.asarray(Vq, dtype=np.float64).reshape(mesh.n_cells, -1)
     cn = mesh.cell_nodes()
-    s_phi = 1.0 / np.sqrt(M)
-    # S X on phi nodes, zero on the nodes that carry no psi unknown
-    SX = np.zeros((mesh.n_phi, X.shape[1]))
-    ids = mesh.psi_to_phi()
-    SX[ids] = s_phi[ids][:, None] * X
+    off = mesh.NX * mesh.NY * mesh.gz_lo
     NX, NY = mesh.NX, mesh.NY
     for r, I in enumerate(rows):
-        g = int(ids[I])
+        g = int(I) + off
         gx, gy, gz = g % NX, (g // NX) % NY, g // (NX * NY)
         acc = np.zeros(X.shape[1])
         for e, l in mesh.node_cells(gx, gy, gz):
+            nodes = cn[e]
+            psi = nodes - off
+            ok = (psi >= 0) & (psi < mesh.n_psi)
+            sx = np.zeros((len(nodes), X.shape[1]))
+            sx[ok] = X[psi[ok]].astype(np.float64) / np.sqrt(M[nodes[ok]])[:, None]
             Ve_row = (B[:, l] * W * Vq[e]) @ B          # V_e[l, :]
-            acc += Ve_row @ SX[cn[e]]
-        out[r] += s_phi[g] * acc
+            acc += Ve_row @ sx
+        out[r] += acc / np.sqrt(M[g])
     return out

@@ -153,6 +153,21 @@ class Mesh:
         assert veff.dtype == torch.float64 and veff.is_cuda and veff.numel() == self.n_psi
         call("fe_set_potential", self._h, _ptr(veff.contiguous()))
 
+    def set_potential_quad(self, vq):
+        """V_eff at every cell's Gauss points, [n_cells, (p+1)^3] float64 on the device
+        (fe_set_potential_quad): the potential term integrated by Gauss quadrature."""
+        assert vq.dtype == torch.float64 and vq.is_cuda
+        assert vq.numel() == self.n_cells * (self.p + 1) ** 3
+        call("fe_set_potential_quad", self._h, _ptr(vq.contiguous()))
+
+    def interp_quad(self, f_phi):
+        """Values at every cell's Gauss points of the phi-node field f_phi (fe_interp_quad)."""
+        assert f_phi.dtype == torch.float64 and f_phi.is_cuda and f_phi.numel() == self.n_phi
+        out = torch.empty((self.n_cells, (self.p + 1) ** 3), dtype=torch.float64,
+                          device=f_phi.device)
+        call("fe_interp_quad", self._h, _ptr(f_phi.contiguous()), _ptr(out))
+        return out
+
     def apply_H(self, X, Y=None, prec=FE_F64):
         n, nvec = X.shape[0], X.shape[1]
         assert n == self.n_psi and X.dtype == self._block_dtype(prec) and X.is_cuda

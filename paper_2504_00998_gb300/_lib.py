@@ -34,7 +34,7 @@ EXPORTS = [
     "fe_batch_create", "fe_batch_destroy", "fe_batch_apply_H", "fe_batch_cheb_filter",
     "fe_batch_rayleigh_ritz", "fe_density", "fe_occupations", "fe_mixer_create",
     "fe_mixer_destroy", "fe_mixer_step", "fe_lda_exchange", "fe_planar", "fe_dipole", "fe_vbare_phi",
-    "fe_set_nonlocal", "fe_set_kpoint",
+    "fe_set_nonlocal", "fe_set_kpoint", "fe_set_potential_quad", "fe_interp_quad",
 ]
 
 
@@ -92,6 +92,8 @@ def load(path=LIB_PATH):
         "fe_poisson_apply_K_f32": ([P, P, P], I),
         "fe_lda_exchange": ([P, P, P, C.POINTER(D)], I),
         "fe_set_kpoint": ([P, D, D], I),
+        "fe_set_potential_quad": ([P, P], I),
+        "fe_interp_quad": ([P, P, P], I),
         "fe_poisson_rhs": ([P, P, P, P, P], I),
         "fe_rayleigh_ritz": ([P, P, I64, I64, P, I], I),
         "fe_lanczos_bounds": ([P, P, I, C.POINTER(D), C.POINTER(D)], I),

@@ -58,6 +58,9 @@ fe_status check_blocks(const fe_batch* b, const void* const* X, const int64_t* n
                      "a multiple of 16", what, i, eb);
     if (!b->meshes[i]->has_potential)
       return fe_fail(FE_EINVAL, "%s: instance %zu: call fe_set_potential first", what, i);
+    if (b->meshes[i]->has_quad || b->meshes[i]->has_k || b->meshes[i]->nl.natoms > 0)
+      return fe_fail(FE_EUNSUPPORTED, "%s: instance %zu: batched operators take the Gamma-point "
+                     "local operator with a collocated potential only", what, i);
   }
   return FE_OK;
 }
@@ -194,6 +197,8 @@ extern "C" fe_status fe_batch_create(fe_mesh* const* meshes, int n, fe_batch** o
       return fe_fail(FE_EUNSUPPORTED, "fe_batch_create: mesh %d carries the nonlocal term", i);
     if (meshes[i]->has_k)
       return fe_fail(FE_EUNSUPPORTED, "fe_batch_create: mesh %d has a Bloch wave vector", i);
+    if (meshes[i]->has_quad)
+      return fe_fail(FE_EUNSUPPORTED, "fe_batch_create: mesh %d has a quadrature potential", i);
   }
   for (int i = 1; i < n; ++i) {
     const fe_mesh* m = meshes[i];

@@ -60,14 +60,17 @@ fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t 
       FE_TRY(fe::kron_f64(m->coefH, g, io, m->stream));
       KronIO<double> ia{(const double*)X, ld, (double*)Y, ld, (const double*)Y, ld, nullptr,
                         nvec, alpha, 1.0, 0.0};
-      return fe::kron_f64(m->coefA, g, ia, m->stream);
+      FE_TRY(fe::kron_f64(m->coefA, g, ia, m->stream));
+    } else {
+      KronIO<float> io{(const float*)X, ld, (float*)Y, ld, (const float*)Z, ld, m->d_veff_f,
+                       nvec, (float)alpha, (float)beta, (float)sh};
+      FE_TRY(fe::kron_f32(m->coefH, g, io, m->stream));
+      KronIO<float> ia{(const float*)X, ld, (float*)Y, ld, (const float*)Y, ld, nullptr, nvec,
+                       (float)alpha, 1.0f, 0.0f};
+      FE_TRY(fe::kron_f32(m->coefA, g, ia, m->stream));
     }
-    KronIO<float> io{(const float*)X, ld, (float*)Y, ld, (const float*)Z, ld, m->d_veff_f, nvec,
-                     (float)alpha, (float)beta, (float)sh};
-    FE_TRY(fe::kron_f32(m->coefH, g, io, m->stream));
-    KronIO<float> ia{(const float*)X, ld, (float*)Y, ld, (const float*)Y, ld, nullptr, nvec,
-                     (float)alpha, 1.0f, 0.0f};
-    return fe::kron_f32(m->coefA, g, ia, m->stream);
+    // the real symmetric quadrature potential acts on the (re, im) lanes alike
+    return fe_quad_apply(m, X, Y, nvec, ld, alpha, prec == FE_F64);
   }
   if (prec == FE_F64) {
     KronIO<double> io{(const double*)X, ld, (double*)Y, ld, (const double*)Z, ld, m->d_veff,
@@ -81,6 +84,7 @@ fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t 
     FE_TRY(fe_tc_apply(m, (const float*)X, (float*)Y, (const float*)Z, nvec, ld, (float)alpha,
                        (float)beta, (float)shift, prec));
   }
+  FE_TRY(fe_quad_apply(m, X, Y, nvec, ld, alpha, prec == FE_F64));
   return fe_nonlocal_apply(m, X, Y, nvec, ld, alpha, prec == FE_F64);
 }
 

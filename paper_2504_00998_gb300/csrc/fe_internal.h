@@ -214,6 +214,14 @@ struct fe_mesh {
   // Poisson arithmetic: 0 double CG, 1 float corrections with double residuals
   int poisson_arith = 1;
   FeNonlocal nl;            // nonlocal term (natoms == 0: none)
+  // potential by Gauss quadrature (fe_quadpot.cu): Bq[q][i] = l_i(gauss point q), wq the
+  // Gauss weights (p + 1 points); W = w |J| V at every cell's Gauss points; M^-1/2 at psi nodes
+  double Bq[FE_MAXN1][FE_MAXN1] = {}, wq[FE_MAXN1] = {};
+  bool has_quad = false;
+  double* d_qW = nullptr;
+  float* d_qW_f = nullptr;
+  double* d_rsq = nullptr;
+  float* d_rsq_f = nullptr;
 
   // cached coarse-space inverse (WS_PCOARSE): valid for the constraint set of pc_key
   int pc_state = 0;          // 0 none, 1 valid, 2 not SPD (Jacobi only for this key)
@@ -248,6 +256,12 @@ KronGeom fe_geom(const fe_mesh* m, bool psi);
 fe_status fe_nonlocal_apply(fe_mesh* m, const void* X, void* Y, int64_t nvec, int64_t ld,
                             double alpha, bool dbl);
 void fe_nonlocal_free(fe_mesh* m);
+// potential by Gauss quadrature -- fe_quadpot.cu: Y += alpha M^-1/2 V_quad M^-1/2 X (no-op
+// unless fe_set_potential_quad is in effect); basis tables at mesh creation; release
+fe_status fe_quad_apply(fe_mesh* m, const void* X, void* Y, int64_t nvec, int64_t ld,
+                        double alpha, bool dbl);
+void fe_quad_setup_basis(fe_mesh* m);
+void fe_quad_free(fe_mesh* m);
 
 // fields (potentials, densities) -- fe_fields.cu
 fe_status fe_fields_build(fe_mesh* m);

@@ -262,6 +262,7 @@ extern "C" fe_status fe_mesh_create(const fe_mesh_desc* d, fe_mesh** out) {
   m->J = m->h[0] * m->h[1] * m->h[2] / 8.0;
   gll_rule(m->p, m->xi, m->w);
   element_matrices(m);
+  fe_quad_setup_basis(m);
   build_coef(m, true, &m->coefH);
   build_coef(m, false, &m->coefK);
 
@@ -313,6 +314,7 @@ extern "C" fe_status fe_mesh_destroy(fe_mesh* m) {
   cudaStreamSynchronize(m->stream);
   for (int i = 0; i < FE_NWS; ++i) if (m->ws[i]) cudaFree(m->ws[i]);
   fe_nonlocal_free(m);
+  fe_quad_free(m);
   if (m->tc_err_pinned) cudaFreeHost(m->tc_err_pinned);
   cudaFree(m->d_veff);
   cudaFree(m->d_veff_f);
@@ -415,6 +417,7 @@ extern "C" fe_status fe_set_potential(fe_mesh* m, const double* veff) {
   k_d2f<<<nb, 256, 0, m->stream>>>(m->d_veff, m->d_veff_f, m->n_psi); fe_count_launch();
   FE_CUDA(cudaGetLastError());
   m->has_potential = true;
+  m->has_quad = false;   // back to the collocated potential
   return FE_OK;
 }
 
