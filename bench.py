@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--prec", choices=["f32", "f64", "bf16"], default="f32")
     ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep", "p5nl", "scf", "p5k",
-                                           "p5q"],
+                                           "p5q", "p5qs"],
                     default="p5",
                     help="p5: the benchmark slab; p5s / p3: smaller slabs; sweep: the batched "
                          "bias sweep of 24 independent 8x8xH-cell p=4 slabs; p5nl: the "
@@ -51,7 +51,8 @@ def parse():
                          "scf: self-consistent iterations on the benchmark slab; p5k: the "
                          "benchmark step at a Bloch wave vector (complex block of the same "
                          "size); p5q: the benchmark step with the potential integrated by "
-                         "Gauss quadrature (V_bare interpolated to the Gauss points)")
+                         "Gauss quadrature (V_bare interpolated to the Gauss points); p5qs: "
+                         "p5q on the p5s slab")
     ap.add_argument("--rr", choices=["f64", "tc32"], default="tc32",
                     help="Rayleigh-Ritz block products for float storage: double GEMMs or "
                          "FP32-accurate tensor-core emulation (n x n part always double)")
@@ -65,7 +66,7 @@ def workload(name):
     256 vectors (a 0.5 GB block, above L2) for profiler captures; p3: the small CEF slab."""
     if name in ("p5", "p5nl", "scf", "p5k", "p5q"):
         return W.config2()
-    if name == "p5s":
+    if name in ("p5s", "p5qs"):
         s = W.config2()
         return W.Slab(s.name.replace("96", "32") + "-short", (s.L[0], s.L[1], 32.0),
                       (16, 16, 16), 5, s.R - np.array([0.0, 0.0, 32.0]), s.Z, s.bias, nvec=256,
@@ -322,7 +323,8 @@ def run_gpu(args):
         na = len(slab.R)
         m.set_nonlocal(slab.R, np.full(na, 0.8), np.tile([1.0, 0.4, 0.4, 0.4], (na, 1)), 2.6)
         nl_desc = f" + synthetic s,p nonlocal projectors on all {na} atoms (sigma 0.8, cut 2.6 bohr)"
-    if args.workload == "p5q":
+    quad = args.workload in ("p5q", "p5qs")
+    if quad:
         nl_desc = (f" with the potential integrated by {slab.p + 1}^3-point Gauss quadrature "
                    "(V_bare interpolated to the Gauss points)")
     phi = torch.empty(m.n_phi, dtype=torch.float64, device=dev)
@@ -330,7 +332,7 @@ def run_gpu(args):
 
     def set_pot():
         # V_eff at the psi nodes (collocated), or at every cell's Gauss points
-        if args.workload == "p5q":
+        if quad:
             m.set_potential_quad(m.interp_quad(m.vbare_phi(phi, slab.bias)))
         else:
             m.set_potential(vb)
@@ -484,7 +486,7 @@ def run_gpu(args):
 
     cpu = None
     if (rank == 0 and world == 1 and not args.no_cpu_baseline
-            and args.workload not in ("p5k", "p5q")):
+            and args.workload not in ("p5k", "p5q", "p5qs")):
         cpu = cpu_baseline_oracle(slab, nvec)
         cpu.pop("seconds", None)
 

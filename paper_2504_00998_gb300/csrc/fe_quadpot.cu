@@ -18,7 +18,10 @@
 #include <cmath>
 #include <vector>
 
+#include <type_traits>
+
 #include "fe_blas.cuh"
+#include "fe_gll_tables.h"
 #include "fe_internal.h"
 
 namespace {
@@ -123,7 +126,15 @@ __device__ __forceinline__ void contract(const QuadB<T>& cb, const T* __restrict
   for (int q = 0; q < N1; ++q) {
     V acc = vzero<V>();
 #pragma unroll
-    for (int e = 0; e < N1; ++e) acc = vfma(TR ? cb.B[e][q] : cb.B[q][e], in[e], acc);
+    for (int e = 0; e < N1; ++e) {
+      // float: the interpolation table as compile-time constants (immediate operands)
+      T c;
+      if constexpr (std::is_same<T, float>::value)
+        c = TR ? fe::gauss_b<P>(e, q) : fe::gauss_b<P>(q, e);
+      else
+        c = TR ? cb.B[e][q] : cb.B[q][e];
+      acc = vfma(c, in[e], acc);
+    }
     if constexpr (WEIGH) acc = vscale(Ws[base + q * STRIDE], acc);
     d[(base + q * STRIDE) * G + grp] = acc;
   }

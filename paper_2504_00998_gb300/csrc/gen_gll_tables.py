@@ -1,11 +1,13 @@
-"""Writes fe_gll_tables.h: the shape-only 1D tables of the float Hamiltonian operator kernel.
+"""Writes fe_gll_tables.h: the shape-only 1D tables of the float Hamiltonian operator kernel
+and of the float Gauss-quadrature potential kernel.
 
 For degree p the in-plane contractions of the mass-scaled operator use
   MS[j][k] = M1[j][k] sig_k,   KS[j][k] = K1[j][k] sig_k,
 with M1, K1 the exactly integrated 1D mass and stiffness matrices of the Lagrange basis on the
 p + 1 Gauss-Lobatto-Legendre nodes of [-1, 1] and sig_k = 1 / sqrt(m_k) (m_k = w_k, or 2 w_0 at
 a node shared by two cells).  They depend on p only; the mesh enters through the scalars
-ax, ay at run time.  The rules are computed the way the library's mesh set-up computes them
+ax, ay at run time.  GB[q][i] = l_i(g_q) interpolates from the GLL nodes to the p + 1
+Gauss-Legendre points g_q of [-1, 1] (the potential integrated by Gauss quadrature).  The rules are computed the way the library's mesh set-up computes them
 (three-term Legendre recurrence, Newton from the same starting points, (p+1)-point Gauss
 quadrature of the products) and rounded to float.
 
@@ -87,6 +89,12 @@ def tables(p):
     return MS, KS
 
 
+def gauss_interp(p):
+    xi, _ = gll_rule(p)
+    gq = sorted(gauss_rule(p + 1)[0])   # ascending, as the points of a cell are ordered
+    return [[lagrange(xi, i, gq[q])[0] for i in range(p + 1)] for q in range(p + 1)]
+
+
 def f32(v):
     import struct
     return struct.unpack("f", struct.pack("f", v))[0]
@@ -99,12 +107,14 @@ def emit(name, A):
 
 def main():
     out = ["// Generated by gen_gll_tables.py (do not edit): shape-only 1D tables M1 sig and K1 sig",
-           "// of the float Hamiltonian operator for p = 1..6 (see the script for their definition).",
+           "// of the float Hamiltonian operator and the GLL-to-Gauss interpolation GB for",
+           "// p = 1..6 (see the script for their definition).",
            "#pragma once", "", "namespace fe {", ""]
     for p in range(1, 7):
         MS, KS = tables(p)
         out.append(emit(f"kGllMS{p}", MS))
         out.append(emit(f"kGllKS{p}", KS))
+        out.append(emit(f"kGaussB{p}", gauss_interp(p)))
     out.append("""// MS[j][k] and KS[j][k] of degree P (compile-time indices fold to immediates)
 template <int P>
 __device__ __forceinline__ constexpr float gll_ms(int j, int k) {
@@ -123,6 +133,16 @@ __device__ __forceinline__ constexpr float gll_ks(int j, int k) {
   else if constexpr (P == 4) return kGllKS4[j][k];
   else if constexpr (P == 5) return kGllKS5[j][k];
   else return kGllKS6[j][k];
+}
+// GB[q][i] of degree P
+template <int P>
+__device__ __forceinline__ constexpr float gauss_b(int q, int i) {
+  if constexpr (P == 1) return kGaussB1[q][i];
+  else if constexpr (P == 2) return kGaussB2[q][i];
+  else if constexpr (P == 3) return kGaussB3[q][i];
+  else if constexpr (P == 4) return kGaussB4[q][i];
+  else if constexpr (P == 5) return kGaussB5[q][i];
+  else return kGaussB6[q][i];
 }
 
 }  // namespace fe""")
