@@ -182,38 +182,43 @@ k_quad_apply(const QuadB<T> cb, const QuadPass g, const T* __restrict__ X, T* __
     Ws[e] = W[cell * NN + e];
   }
   __syncthreads();
-  // u = M^-1/2 X on the cell's nodes: every 16-byte load of the thread is issued before the
-  // first is used (zero on Dirichlet faces and past the last vector; a row holds ld >= the
-  // group's end, so the whole group is in bounds)
-  {
-    V r[IT];
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int sl = tid + it * NT;
-      r[it] = vzero<V>();
-      if (sl < SLOTS) {
-        const int e = sl / G, vv = (sl % G) * VW;
-        const int64_t n = node[e];
-        if (n >= 0 && v0 + vv < nvec) r[it] = *reinterpret_cast<const V*>(X + n * ld + v0 + vv);
-      }
-    }
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-      const int sl = tid + it * NT;
-      if (sl < SLOTS) {
-        const int e = sl / G, vv = (sl % G) * VW;
-        const int64_t left = nvec - (v0 + vv);
-        V u = vscale(rs[e], r[it]);
-        if (left < VW) u = vkeep(u, left > 0 ? (int)left : 0);
-        reinterpret_cast<V*>(bufA)[sl] = u;
-      }
-    }
-  }
-  __syncthreads();
   const bool act = tid < S::LINES;
   const int grp = tid % G, ab = tid / G;
-  const int la = ab % N1, lb = ab / N1;
-  if (act) contract<T, P, 0, false, false>(cb, bufA, bufB, Ws, la, lb, grp);
+  const int la = ab % N1, lb = ab / N1;     // (j, k) of the thread's x line
+  const int xbase = (lb * N1 + la) * N1;
+  const int64_t vv = v0 + (int64_t)grp * VW;
+  const int64_t left = nvec - vv;           // lanes of the group that are vectors
+  // x lines straight from global memory: u = M^-1/2 X on the line's nodes (every load of
+  // the thread in flight before the first use; zero on Dirichlet faces and past the last
+  // vector; a row holds ld >= the group's end, so the whole group is in bounds), then the
+  // forward x contraction
+  if (act) {
+    V in[N1];
+#pragma unroll
+    for (int e = 0; e < N1; ++e) {
+      const int64_t n = node[xbase + e];
+      in[e] = vzero<V>();
+      if (n >= 0 && left > 0) in[e] = *reinterpret_cast<const V*>(X + n * ld + vv);
+    }
+    V* d = reinterpret_cast<V*>(bufB);
+#pragma unroll
+    for (int e = 0; e < N1; ++e) {
+      in[e] = vscale(rs[xbase + e], in[e]);
+      if (left < VW) in[e] = vkeep(in[e], left > 0 ? (int)left : 0);
+    }
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      V acc = vzero<V>();
+#pragma unroll
+      for (int e = 0; e < N1; ++e) {
+        T c;
+        if constexpr (std::is_same<T, float>::value) c = fe::gauss_b<P>(q, e);
+        else c = cb.B[q][e];
+        acc = vfma(c, in[e], acc);
+      }
+      d[(xbase + q) * G + grp] = acc;
+    }
+  }
   __syncthreads();
   if (act) contract<T, P, 1, false, false>(cb, bufB, bufA, Ws, la, lb, grp);
   __syncthreads();
@@ -223,6 +228,51 @@ k_quad_apply(const QuadB<T> cb, const QuadPass g, const T* __restrict__ X, T* __
   __syncthreads();
   if (act) contract<T, P, 1, true, false>(cb, bufA, bufB, Ws, la, lb, grp);
   __syncthreads();
+  if (!g.foldy) {
+    // transposed x contraction in registers and Y += alpha M^-1/2 (.) along the line; a
+    // single cell along x (foldx) adds its two copies of node 0 before writing it once
+    if (act) {
+      const V* sv = reinterpret_cast<const V*>(bufB);
+      V in[N1], out[N1];
+#pragma unroll
+      for (int q = 0; q < N1; ++q) in[q] = sv[(xbase + q) * G + grp];
+#pragma unroll
+      for (int e = 0; e < N1; ++e) {
+        V acc = vzero<V>();
+#pragma unroll
+        for (int q = 0; q < N1; ++q) {
+          T c;
+          if constexpr (std::is_same<T, float>::value) c = fe::gauss_b<P>(q, e);
+          else c = cb.B[q][e];
+          acc = vfma(c, in[q], acc);
+        }
+        out[e] = acc;
+      }
+      if (g.foldx) out[0] = vfma(T(1), out[P], out[0]);
+      V yv[N1];
+#pragma unroll
+      for (int e = 0; e < N1; ++e) {
+        const int64_t n = node[xbase + e];
+        yv[e] = vzero<V>();
+        if (n >= 0 && left > 0 && !(g.foldx && e == P))
+          yv[e] = *reinterpret_cast<const V*>(Y + n * ld + vv);
+      }
+#pragma unroll
+      for (int e = 0; e < N1; ++e) {
+        const int64_t n = node[xbase + e];
+        if (n < 0 || left <= 0 || (g.foldx && e == P)) continue;
+        const V o = vfma(alpha * rs[xbase + e], out[e], yv[e]);
+        T* yp = Y + n * ld + vv;
+        if (left >= VW)
+          *reinterpret_cast<V*>(yp) = o;
+        else
+          vstore_first(yp, o, (int)left);
+      }
+    }
+    return;
+  }
+  // a single cell along y: the two copies of each j = 0 node are in different x lines, so
+  // the block goes back to the nodes in shared memory and is folded there
   if (act) contract<T, P, 0, true, false>(cb, bufB, bufA, Ws, la, lb, grp);
   __syncthreads();
   V* A = reinterpret_cast<V*>(bufA);
@@ -235,16 +285,14 @@ k_quad_apply(const QuadB<T> cb, const QuadPass g, const T* __restrict__ X, T* __
     }
     __syncthreads();
   }
-  if (g.foldy) {
-    for (int idx = tid; idx < N1 * N1 * G; idx += NT) {
-      const int gg = idx % G, r = idx / G;
-      const int i = r % N1, k = r / N1;
-      V x = A[(k * N1 * N1 + i) * G + gg];
-      const V y = A[(k * N1 * N1 + P * N1 + i) * G + gg];
-      A[(k * N1 * N1 + i) * G + gg] = vfma(T(1), y, x);
-    }
-    __syncthreads();
+  for (int idx = tid; idx < N1 * N1 * G; idx += NT) {
+    const int gg = idx % G, r = idx / G;
+    const int i = r % N1, k = r / N1;
+    V x = A[(k * N1 * N1 + i) * G + gg];
+    const V y = A[(k * N1 * N1 + P * N1 + i) * G + gg];
+    A[(k * N1 * N1 + i) * G + gg] = vfma(T(1), y, x);
   }
+  __syncthreads();
   // Y += alpha M^-1/2 (V u): all loads of Y first, then the updates
   {
     V yv[IT];
@@ -253,27 +301,27 @@ k_quad_apply(const QuadB<T> cb, const QuadPass g, const T* __restrict__ X, T* __
       const int sl = tid + it * NT;
       yv[it] = vzero<V>();
       if (sl < SLOTS) {
-        const int e = sl / G, vv = (sl % G) * VW;
+        const int e = sl / G, ww = (sl % G) * VW;
         const int64_t n = node[e];
-        if (n >= 0 && v0 + vv < nvec) yv[it] = *reinterpret_cast<const V*>(Y + n * ld + v0 + vv);
+        if (n >= 0 && v0 + ww < nvec) yv[it] = *reinterpret_cast<const V*>(Y + n * ld + v0 + ww);
       }
     }
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
       const int sl = tid + it * NT;
       if (sl >= SLOTS) continue;
-      const int e = sl / G, vv = (sl % G) * VW;
+      const int e = sl / G, ww = (sl % G) * VW;
       const int i = e % N1, j = (e / N1) % N1;
-      if ((g.foldx && i == P) || (g.foldy && j == P)) continue;
+      if ((g.foldx && i == P) || j == P) continue;
       const int64_t n = node[e];
-      if (n < 0 || v0 + vv >= nvec) continue;
-      const V out = vfma(alpha * rs[e], A[sl], yv[it]);
-      T* yp = Y + n * ld + v0 + vv;
-      const int64_t left = nvec - (v0 + vv);
-      if (left >= VW)
-        *reinterpret_cast<V*>(yp) = out;
+      if (n < 0 || v0 + ww >= nvec) continue;
+      const V o = vfma(alpha * rs[e], A[sl], yv[it]);
+      T* yp = Y + n * ld + v0 + ww;
+      const int64_t rem = nvec - (v0 + ww);
+      if (rem >= VW)
+        *reinterpret_cast<V*>(yp) = o;
       else
-        vstore_first(yp, out, (int)left);
+        vstore_first(yp, o, (int)rem);
     }
   }
 }
