@@ -53,7 +53,7 @@ typedef enum {
   FE_ENOCONV = 4,       /* an iteration hit its cap before the tolerance                */
   FE_EBREAKDOWN = 5,    /* Cholesky of a Gram matrix failed (not positive definite)     */
   FE_ETIMEOUT = 6,      /* reserved: a bounded device wait expired                      */
-  FE_EUNSUPPORTED = 7   /* valid request that this build does not implement             */
+  FE_EUNSUPPORTED = 7   /* valid request that the library does not implement           */
 } fe_status;
 
 /* Arithmetic of the Hamiltonian application.
