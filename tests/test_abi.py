@@ -54,6 +54,12 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.fe_apply_H(None, None, None, 1, 1, 0) == _lib.FE_EINVAL
     assert lib.fe_poisson_solve(None, None, None, None, None, None) == _lib.FE_EINVAL
     assert lib.fe_mesh_destroy(None) == _lib.FE_OK
+    # the variants' entry points reject null meshes and arrays before any CUDA call
+    assert lib.fe_set_potential_quad(None, None) == _lib.FE_EINVAL
+    assert lib.fe_interp_quad(None, None, None) == _lib.FE_EINVAL
+    assert lib.fe_set_kpoint(None, 0.1, 0.2) == _lib.FE_EINVAL
+    assert lib.fe_rayleigh_ritz(None, None, 4, 4, None, 0) == _lib.FE_EINVAL
+    assert lib.fe_lda_exchange(None, None, None, None) == _lib.FE_EINVAL
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
