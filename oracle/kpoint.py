@@ -71,3 +71,35 @@ def hamiltonian_k(mesh, V_psi, k, K=None, M=None):
     n = len(ids)
     return (H0.astype(np.complex128) + 0.5 * (kx * kx + ky * ky) * sp.identity(n, format="csr")
             - 1j * A).tocsr()
+
+
+def apply_Hk_rows(mesh, V_psi, k, X, rows, M=None):
+    """(Ht_k X)[rows, :] from the cell definition, one row at a time (for sizes where the
+    assembled matrix does not fit): the Gamma-point rows of assembly.apply_H_rows, plus
+    1/2 |k|^2 X_I, minus i S_I sum over the cells e touching I of
+    sum_J (kx Gx_e + ky Gy_e)[l_I, J] (S X)_{node_e(J)} (S = M^-1/2, X = 0 on Dirichlet
+    nodes).  X is complex; only the rows the sampled cells touch are promoted."""
+    kx, ky = float(k[0]), float(k[1])
+    M = assembly.lumped_mass(mesh) if M is None else M
+    X = np.asarray(X)
+    Xc = lambda idx: X[idx].astype(np.complex128)
+    re = assembly.apply_H_rows(mesh, V_psi, X.real, rows, M=M)
+    im = assembly.apply_H_rows(mesh, V_psi, X.imag, rows, M=M)
+    out = re + 1j * im
+    Ge = kx * reference_cell_gradient(mesh, 0) + ky * reference_cell_gradient(mesh, 1)
+    cn = mesh.cell_nodes()
+    off = mesh.NX * mesh.NY * mesh.gz_lo
+    NX, NY = mesh.NX, mesh.NY
+    for r, I in enumerate(rows):
+        g = int(I) + off
+        gx, gy, gz = g % NX, (g // NX) % NY, g // (NX * NY)
+        acc = np.zeros(X.shape[1], dtype=np.complex128)
+        for e, l in mesh.node_cells(gx, gy, gz):
+            nodes = cn[e]
+            psi = nodes - off
+            ok = (psi >= 0) & (psi < mesh.n_psi)
+            sx = np.zeros((len(nodes), X.shape[1]), dtype=np.complex128)
+            sx[ok] = Xc(psi[ok]) / np.sqrt(M[nodes[ok]])[:, None]
+            acc += Ge[l] @ sx
+        out[r] += 0.5 * (kx * kx + ky * ky) * Xc(int(I)) - 1j * acc / np.sqrt(M[g])
+    return out

@@ -228,3 +228,30 @@ def test_refused_combinations_and_gamma_reset(fe):
     Y = m.apply_H(torch.tensor(Xr, device="cuda")).cpu().numpy()
     ref = assembly.hamiltonian(om, V) @ Xr
     assert np.linalg.norm(Y - ref) / np.linalg.norm(ref) <= 1e-10
+
+
+def test_full_size_sampled_rows(fe):
+    """The benchmark slab (16 x 16 x 48 cells, p = 5) at k = (0.1, 0.05) with 256 complex
+    float vectors (the block of the benchmark's k-point step): sampled rows of Ht_k X
+    against the oracle's row-by-row form, including rows on the lowest and highest psi
+    planes and on the periodic seams."""
+    import workloads as W
+    slab = W.config2()
+    om = OMesh(slab.L, slab.ncell, slab.p, slab.psi_dirichlet)
+    m = fe.Mesh.from_slab(slab, with_atoms=False)
+    rng = np.random.default_rng(8)
+    V = rng.uniform(-1.0, 0.5, om.n_psi)
+    m.set_potential(torch.tensor(V, device="cuda"))
+    k = (0.1, 0.05)
+    m.set_kpoint(*k)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn((om.n_psi, slab.nvec // 2), generator=gen, device="cuda",
+                    dtype=torch.complex64)
+    Y = m.apply_H(X, prec=fe.FE_F32)
+    NX, NY = om.NX, om.NY
+    plane = NX * NY
+    rows = np.concatenate([[0, NX - 1, plane - 1, om.n_psi - 1, om.n_psi - plane],
+                           rng.integers(0, om.n_psi, 11)])
+    ref = kpoint.apply_Hk_rows(om, V, k, X.cpu().numpy(), rows)
+    got = Y[torch.tensor(rows, device="cuda")].cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-5

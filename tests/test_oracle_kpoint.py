@@ -115,3 +115,19 @@ def test_complex_filter_is_the_polynomial_of_the_spectrum():
         sig = sn
     ref = Q @ (y1[:, None] * (Q.conj().T @ X))
     assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("faces,ncell", [((True, True), (2, 3, 2)), ((False, True), (1, 2, 2)),
+                                         ((True, False), (3, 1, 1))])
+def test_rows_match_the_assembled_operator(faces, ncell):
+    """The row-by-row form (used at sizes where the matrix does not fit) against the
+    assembled Ht_k, including single-cell periodic rows and both face kinds."""
+    om = OMesh((3.0, 3.5, 4.0), ncell, 2, faces)
+    rng = np.random.default_rng(4)
+    V = rng.uniform(-1.0, 1.0, om.n_psi)
+    k = (0.37, -0.21)
+    H = kpoint.hamiltonian_k(om, V, k)
+    X = rng.standard_normal((om.n_psi, 3)) + 1j * rng.standard_normal((om.n_psi, 3))
+    got = kpoint.apply_Hk_rows(om, V, k, X, np.arange(om.n_psi))
+    ref = H @ X
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
