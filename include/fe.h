@@ -150,7 +150,9 @@ fe_status fe_set_nonlocal(fe_mesh* mesh, int natoms, const double* R_host,
  * exact; the |k|^2 term with the lumped overlap), and the blocks of fe_apply_H,
  * fe_cheb_filter and fe_rayleigh_ritz are complex: interleaved (re, im) pairs of float
  * (FE_F32) or double (FE_F64), nvec and ld counting complex entries (16-byte aligned rows).
- * fe_rayleigh_ritz then solves the Hermitian subspace problem in double complex; fe_density
+ * fe_rayleigh_ritz then solves the Hermitian subspace problem (n x n part in double complex;
+ * for float blocks with FE_RR_PRODUCTS_TC32 the block products are real FP32-accurate
+ * tensor-core GEMMs over the (re, im) lanes, else double complex GEMMs); fe_density
  * sums occ_n |u_n|^2 over the complex columns; fe_lanczos_bounds bounds the spectrum of
  * Ht_k.  k = (0, 0) restores the real Gamma-point operator.  Not combined with the nonlocal
  * term, the tensor-core precisions, fe_batch_create or fe_cheb_filter_static
@@ -363,12 +365,15 @@ fe_status fe_poisson_rhs(fe_mesh* mesh, const double* rho_dev, double* f_dev,
 /* Rayleigh-Ritz of span(X) for Ht with orthonormal output: X <- X C with X^T X = I,
  * X^T Ht X = diag(eig), eig_dev[nvec] ascending Ritz values (Section 2.1 orthonormality).
  * Default: C from the Cholesky factor of the scaled Gram matrix and the projected matrix
- * (equivalent to Cholesky-QR then Rayleigh-Ritz); when the Gram matrix is ill-conditioned
+ * (equivalent to Cholesky-QR then Rayleigh-Ritz); when the scaled Gram matrix is
+ * ill-conditioned (cond above 1e8 with double products, 1e4 with tensor-core products)
  * the block is orthonormalised explicitly first (scaled Cholesky-QR2, shifted
- * Cholesky-QR3 on breakdown).  Gram matrices, the projected matrix, factorisations and
- * the rotation are in double precision whatever the storage; float blocks are promoted to
- * a library-owned double workspace.  The one Ht X product runs in double for FE_F64 and in
- * float (sum-factorised) for the float-storage precisions. */
+ * Cholesky-QR3 on breakdown) in double.  The n x n factorisations and eigensolver are in
+ * double; the three block products (Gram matrix, projected matrix, rotation) are double
+ * GEMMs on a library-owned double copy of a float block, or, for float blocks with
+ * FE_OPT_RR_PRODUCTS = FE_RR_PRODUCTS_TC32, FP32-accurate tensor-core GEMMs on the block
+ * itself.  The one Ht X product runs in double for FE_F64 and in float (sum-factorised)
+ * for the float-storage precisions.  Complex (Bloch) blocks: see fe_set_kpoint. */
 fe_status fe_rayleigh_ritz(fe_mesh* mesh, void* X, int64_t nvec, int64_t ld, double* eig_dev,
                            fe_precision prec);
 
