@@ -251,6 +251,11 @@ size_t fe_kcell_scratch_bytes(const fe_mesh* m);
 fe_status fe_kcell_apply_f32(fe_mesh* m, const float* x, float* y);
 fe_status fe_activate(const fe_mesh* m);
 KronGeom fe_geom(const fe_mesh* m, bool psi);
+// Y = alpha (Ht - shift) X + beta Z (plus alpha Ht_nloc X and the quadrature potential when
+// the mesh carries them) in the requested arithmetic; nvec and ld count real lanes
+// (fe_hx.cu)
+fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t nvec, int64_t ld,
+                     double alpha, double beta, double shift, fe_precision prec);
 
 // nonlocal term -- fe_nonlocal.cu: Y += alpha Ht_nloc X; release of the tables
 fe_status fe_nonlocal_apply(fe_mesh* m, const void* X, void* Y, int64_t nvec, int64_t ld,

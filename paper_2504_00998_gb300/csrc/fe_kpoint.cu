@@ -29,9 +29,6 @@
 #include "fe_blas.cuh"
 #include "fe_internal.h"
 
-fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t nvec, int64_t ld,
-                     double alpha, double beta, double shift, fe_precision prec);
-
 namespace {
 
 template <typename T>

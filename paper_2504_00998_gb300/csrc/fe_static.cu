@@ -9,6 +9,7 @@
 // the other streams.  For them, fe_cheb_filter_static keeps the scratch in the file-scope
 // array below instead.  The array is part of the module, so every device that loads this
 // library holds it until the process exits.
+#include <cmath>
 #include <mutex>
 
 #include "fe_internal.h"
@@ -19,16 +20,15 @@
 // a kernel: on the host it is only a stand-in for the symbol, not a device address.
 static __device__ __align__(256) unsigned char fe_static_scratch[FE_STATIC_SCRATCH_BYTES];
 
-fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t nvec, int64_t ld,
-                     double alpha, double beta, double shift, fe_precision prec);
-
 namespace {
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_scratch_mutex;
 void* g_scratch_addr[MAX_DEVICES] = {nullptr};
 
-// device address of the scratch array on the current device (looked up once per device)
+// device address of the scratch array on the current device, looked up once per device and
+// kept for the life of the process (like every other piece of this library's device state,
+// it does not survive cudaDeviceReset)
 fe_status scratch_address(int device, void** out) {
   if (device < 0 || device >= MAX_DEVICES)
     return fe_fail(FE_EINVAL, "fe_cheb_filter_static: device ordinal %d out of range", device);
@@ -64,7 +64,8 @@ extern "C" fe_status fe_cheb_filter_static(fe_mesh* m, void* X, int64_t nvec, in
     return fe_fail(FE_EINVAL, "fe_cheb_filter_static: X must be 16-byte aligned and ld * %d a "
                    "multiple of 16", eb);
   if (degree < 1) return fe_fail(FE_EINVAL, "fe_cheb_filter_static: degree must be >= 1");
-  if (!(a0 < a && a < b)) return fe_fail(FE_EINVAL, "fe_cheb_filter_static: need a0 < a < b");
+  if (!(a0 < a && a < b) || !std::isfinite(a0) || !std::isfinite(b))
+    return fe_fail(FE_EINVAL, "fe_cheb_filter_static: need finite a0 < a < b");
   if (!m->has_potential)
     return fe_fail(FE_EINVAL, "fe_cheb_filter_static: call fe_set_potential first");
   if (m->nl.natoms > 0)
