@@ -187,6 +187,19 @@ fe_status fe_interp_quad(fe_mesh* mesh, const double* f_phi_dev, double* out_dev
 fe_status fe_apply_H(fe_mesh* mesh, const void* X, void* Y, int64_t nvec, int64_t ld,
                      fe_precision prec);
 
+/* Adjoint of fe_apply_H with respect to the potential (Eq. Veff and Hloc: V_eff enters
+ * Ht = 1/2 M^-1/2 K M^-1/2 + diag(V_eff) only through the diagonal term).  Given X and
+ * Ybar = dL/dY for Y = Ht X: gV_dev[I] = sum_v Ybar[I][v] X[I][v], the gradient dL/dV_eff
+ * of the collocated potential.  X, Ybar [n_psi][ld] in the storage type of prec (double
+ * for FE_F64, float otherwise), nvec vectors; complex (Bloch) blocks: nvec and ld count
+ * complex entries and the sum runs over both (re, im) lanes.  gV_dev [n_psi] double,
+ * caller-owned, overwritten.  The adjoint with respect to X is fe_apply_H on Ybar (Ht is
+ * symmetric).  Stream-ordered; deterministic (fixed summation order).  FE_EINVAL for null
+ * arguments or nvec > ld; FE_EUNSUPPORTED while the Gauss-quadrature potential
+ * (fe_set_potential_quad) is in effect. */
+fe_status fe_potential_vjp(fe_mesh* mesh, const void* X, const void* Ybar, int64_t nvec,
+                           int64_t ld, double* gV_dev, fe_precision prec);
+
 /* In-place degree-m scaled Chebyshev filter of X (Zhou & Saad three-term recurrence):
  * X <- T_m((Ht - c)/e) X / T_m((a0 - c)/e), e = (b - a)/2, c = (b + a)/2, a0 < a < b;
  * degree counts applications of Ht.  Uses one library-owned workspace of X's size. */
@@ -203,7 +216,10 @@ fe_status fe_cheb_filter(fe_mesh* mesh, void* X, int64_t nvec, int64_t ld, int d
  * library, so n_psi * ld * sizeof(element) must not exceed 64 MiB (FE_EINVAL otherwise).
  * The call performs no cudaMalloc / cudaFree and no allocating library call.
  * Set-up: the first call on a device looks up the array's device address with that device
- * current (cudaGetSymbolAddress); make that first call before any stream capture.
+ * current (cudaGetSymbolAddress); make that first call before any stream capture.  The
+ * address is kept for the life of the process: like the meshes and their workspaces, it
+ * does not survive cudaDeviceReset.  a0, a and b as for fe_cheb_filter (finite,
+ * a0 < a < b; FE_EINVAL otherwise).
  * Sharing: every call on a device uses that device's one copy of the array, which keeps
  * the last call's contents (the filter writes the scratch before reading it, so stale
  * contents never matter); calls that overlap on the GPU, for example on two streams or two
@@ -323,7 +339,9 @@ typedef struct { int iters; double rel_residual; int status; } fe_solve_info;
  *   vbare_dev optional output [n_psi]: phi + V_loc - V_sm + V_app at psi nodes, i.e. the
  *             V_eff of this library (Section 3.2 calls it V_bare).
  *   info      optional: iterations, final relative residual, status.
- * Returns FE_ENOCONV if max_iter is reached first. */
+ * Returns FE_ENOCONV if max_iter is reached first, and FE_EINVAL (before any iteration)
+ * when the initial residual is not finite: a NaN or infinity in rho, the atoms or the
+ * constraint values. */
 fe_status fe_poisson_solve(fe_mesh* mesh, const double* rho_dev, const fe_poisson_bc* bc,
                            double* phi_dev, double* vbare_dev, fe_solve_info* info);
 
@@ -373,7 +391,9 @@ fe_status fe_poisson_rhs(fe_mesh* mesh, const double* rho_dev, double* f_dev,
  * GEMMs on a library-owned double copy of a float block, or, for float blocks with
  * FE_OPT_RR_PRODUCTS = FE_RR_PRODUCTS_TC32, FP32-accurate tensor-core GEMMs on the block
  * itself.  The one Ht X product runs in double for FE_F64 and in float (sum-factorised)
- * for the float-storage precisions.  Complex (Bloch) blocks: see fe_set_kpoint. */
+ * for the float-storage precisions.  Complex (Bloch) blocks: see fe_set_kpoint.
+ * FE_EBREAKDOWN, with X unchanged, when a column of X is zero or not finite; FE_EBREAKDOWN
+ * also when the shifted Cholesky-QR3 fallback cannot orthonormalise a rank-deficient block. */
 fe_status fe_rayleigh_ritz(fe_mesh* mesh, void* X, int64_t nvec, int64_t ld, double* eig_dev,
                            fe_precision prec);
 
@@ -403,7 +423,10 @@ fe_status fe_atom_fields_vjp(fe_mesh* mesh, const double* g_rho_dev, const doubl
                              const double* g_vlms_dev, double* dR_host);
 
 /* k-step Lanczos on Ht from the start vector v0_dev[n_psi] (Zhou & Li bounds):
- * *lo = smallest Ritz value, *hi = largest Ritz value + ||f_k||.  Synchronises. */
+ * *lo = smallest Ritz value, *hi = largest Ritz value + ||f_k||.  Synchronises.
+ * FE_EINVAL for a zero or non-finite start vector; FE_EBREAKDOWN when the Krylov space
+ * becomes invariant before the last step (beta_j <= 1e-10 of the largest alpha / beta so
+ * far: v0 lies in an invariant subspace, and no bound of the whole spectrum follows). */
 fe_status fe_lanczos_bounds(fe_mesh* mesh, const double* v0_dev, int steps, double* lo,
                             double* hi);
 

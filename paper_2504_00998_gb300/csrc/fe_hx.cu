@@ -189,7 +189,9 @@ __global__ void k_sqrt(double* x) { *x = sqrt(*x); }
 __global__ void k_lz_shift(const double* __restrict__ f, double* __restrict__ v,
                            double* __restrict__ vold, const double* __restrict__ beta, int64_t n,
                            int inc) {
-  double s = 1.0 / *beta;
+  // (an exactly invariant Krylov space, beta = 0, leaves v = 0; the host reports it)
+  const double b = *beta;
+  const double s = b > 0.0 ? 1.0 / b : 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     vold[inc * i] = v[inc * i];
@@ -276,7 +278,30 @@ extern "C" fe_status fe_lanczos_bounds(fe_mesh* m, const double* v0, int steps, 
   std::vector<double> d(hs.begin(), hs.begin() + steps);
   std::vector<double> e(hs.begin() + steps, hs.begin() + 2 * steps - 1);
   double fnorm = hs[2 * steps - 1];
+  for (double x : hs)
+    if (!std::isfinite(x))
+      return fe_fail(FE_EINVAL, "fe_lanczos_bounds: the start vector is zero or not finite");
+  // Breakdown: beta_j ~ 0 before the last step means that v0 lies in an invariant subspace
+  // of Ht; the Krylov space then never sees the rest of the spectrum, so theta_max + |f| is
+  // no bound of it
+  // (j + 1 steps spanning the whole space of nl unknowns is the one exact exception: the
+  // tridiagonal matrix then holds the whole spectrum)
+  double scale = 0.0;
+  for (int j = 0; j + 1 < steps; ++j) {
+    scale = std::fmax(scale, std::fabs(d[j]));
+    if (j) scale = std::fmax(scale, e[j - 1]);
+    if (e[j] > 1e-10 * scale) continue;
+    if (j + 1 >= nl) {
+      d.resize(j + 1);
+      e.resize(j);
+      fnorm = 0.0;
+      break;
+    }
+    return fe_fail(FE_EBREAKDOWN, "fe_lanczos_bounds: breakdown at step %d (the start "
+                   "vector lies in an invariant subspace of Ht); use a start vector with "
+                   "components along the whole spectrum, e.g. a random one", j + 1);
+  }
   *lo = tridiag_eig(d, e, 0);
-  *hi = tridiag_eig(d, e, steps - 1) + fnorm;
+  *hi = tridiag_eig(d, e, (int)d.size() - 1) + fnorm;
   return FE_OK;
 }

@@ -1344,6 +1344,13 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   };
   double rr = 0.0;
   FE_TRY(residual(&rr));
+  if (!std::isfinite(rr)) {
+    // a NaN or infinity in rho, the atoms or the constraint values: no iteration can mean
+    // anything, so report it instead of running to the iteration cap
+    if (info) { info->iters = 0; info->rel_residual = rr; info->status = FE_EINVAL; }
+    return fe_fail(FE_EINVAL, "Poisson: the initial residual is not finite (NaN or infinity "
+                   "in the density, the atoms or the constraint values)");
+  }
   const double bnorm2 = rr;
   const double tol2 = bc->rtol * bc->rtol * bnorm2;
   int used = 0;

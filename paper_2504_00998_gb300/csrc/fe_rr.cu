@@ -26,9 +26,6 @@
 #include "fe_blas.cuh"
 #include "fe_internal.h"
 
-fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t nvec, int64_t ld,
-                     double alpha, double beta, double shift, fe_precision prec);
-
 // the lower triangle of a SYRK result (upper stored) is filled in (defined below)
 __global__ void k_fill_lower(double* __restrict__ S, int n);
 
@@ -178,11 +175,18 @@ fe_status rr_small(fe_mesh* m, int64_t nvec, RrWs& w, double* eig, bool* ill, do
   FE_CUSOLVER(cusolverDnDpotrf(m->cusolver, CUBLAS_FILL_MODE_UPPER, n, w.S, n, w.work, w.lwork,
                                w.info));
   k_diag<<<(n + 255) / 256, 256, 0, st>>>(w.S, n, w.eig); fe_count_launch();
-  std::vector<double> rdiag(n);
+  std::vector<double> rdiag(n), dinv(n);
   int hinfo = 0;
   FE_CUDA(cudaMemcpyAsync(&hinfo, w.info, sizeof(int), cudaMemcpyDeviceToHost, st));
   FE_CUDA(cudaMemcpyAsync(rdiag.data(), w.eig, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  FE_CUDA(cudaMemcpyAsync(dinv.data(), w.d, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   FE_CUDA(cudaStreamSynchronize(st));
+  // a zero column (or a NaN / infinity in one) makes the block rank deficient whatever the
+  // orthonormalisation: report it before any pass scales the block by 1 / |column|
+  for (int j = 0; j < n; ++j)
+    if (!std::isfinite(dinv[j]))
+      return fe_fail(FE_EBREAKDOWN, "fe_rayleigh_ritz: column %d of the block is zero or not "
+                     "finite (rank-deficient block)", j);
   if (hinfo != 0) { *ill = true; return FE_OK; }
   double rmax = 0.0, rmin = 1e300;
   for (int j = 0; j < n; ++j) {

@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import workloads as W
+from entrywise import assert_operator_entries
 from oracle import assembly, chefsi, poisson, potentials
 from oracle.mesh import Mesh as OMesh
 
@@ -62,6 +63,17 @@ def test_cef_slab_end_to_end(fe):
     evf = m.rayleigh_ritz(Xf, prec=fe.FE_F32).cpu().numpy()
     k = min(int(slab.n_electrons // 2), slab.nvec - 8)
     assert np.max(np.abs(evf[:k] - ev_ref[:k])) <= 1e-5
+    # the tensor-core filter (bf16 operands, fp32 accumulation) with the same float
+    # Rayleigh-Ritz: its one rounding of the cell matrix K_e moves the filtered subspace at
+    # first order, so the Ritz values miss the 1e-5 Ha criterion by three orders of
+    # magnitude (measured on GB300: 1.24e-2 Ha; the gap is asserted, not hidden)
+    Xb = torch.tensor(X0, dtype=torch.float32, device="cuda")
+    m.cheb_filter(Xb, slab.degree, a, hi, lo, prec=fe.FE_BF16_F32ACC)
+    evb = m.rayleigh_ritz(Xb, prec=fe.FE_BF16_F32ACC).cpu().numpy()
+    err_bf16 = np.max(np.abs(evb[:k] - ev_ref[:k]))
+    print(f"config 1 Ritz error: float {np.max(np.abs(evf[:k] - ev_ref[:k])):.3e}, "
+          f"bf16 tensor-core filter {err_bf16:.3e} Ha")
+    assert err_bf16 <= 3e-2
 
 
 def test_p5_slab_sampled_rows(fe):
@@ -80,13 +92,48 @@ def test_p5_slab_sampled_rows(fe):
     Ke = assembly.reference_cell_stiffness(om)
     M = assembly.lumped_mass(om)
     ref = assembly.apply_H_rows(om, V, X0, rows, Ke=Ke, M=M)
-    for prec, tol in ((fe.FE_F64, 1e-10), (fe.FE_F32, 2e-5)):
+    # entry bound: the magnitudes of the terms, sum_e |K_e| |S X| and |V| |X|, row by row
+    mag = assembly.apply_H_rows(om, np.abs(V), np.abs(X0), rows, Ke=np.abs(Ke), M=M)
+    for prec, tol, etol in ((fe.FE_F64, 1e-10, 1e-13), (fe.FE_F32, 2e-5, 1e-6)):
         Xg = torch.tensor(X0, dtype=fe.storage_dtype(prec), device="cuda")
         Y = m.apply_H(Xg, prec=prec)
         got = Y[torch.tensor(rows, device="cuda")].double().cpu().numpy()
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol, prec
+        assert_operator_entries(got, ref, mag, etol, f"p = 5 slab rows, precision {prec}")
         del Xg, Y
         torch.cuda.empty_cache()
+
+
+def test_p5_slab_mixed_eigenvalues_vs_fp64(fe):
+    """The benchmark's accuracy criterion as a test: on the p = 5 slab (1.53 M psi nodes,
+    512 vectors, degree 30), two filter + Rayleigh-Ritz cycles from the same start block in
+    the float path (FP32 operator, FP32-accurate tensor-core block products, double n x n
+    part) and in FP64 agree to 1e-5 Ha over the lowest 384 Ritz values; the bf16
+    tensor-core filter's gap is measured and bounded."""
+    slab = W.config2()
+    m = fe.Mesh.from_slab(slab)
+    _, vb, info = m.poisson_solve(slab.bias, rtol=1e-10)
+    assert info.status == 0
+    m.set_potential(vb)
+    lo, hi = m.lanczos_bounds(torch.tensor(W.lanczos_start(m.n_psi), device="cuda"), 20)
+    a = lo + R_FILTER * (hi - lo)
+    X0 = torch.from_numpy(W.start_block(slab))
+    k = min(int(slab.n_electrons // 2), slab.nvec - 8)
+    ev = {}
+    for prec, tc in ((fe.FE_F64, False), (fe.FE_F32, True), (fe.FE_BF16_F32ACC, True)):
+        m.set_rr_products(tc)
+        X = X0.to("cuda", fe.storage_dtype(prec))
+        for _ in range(2):
+            m.cheb_filter(X, slab.degree, a, hi, lo, prec=prec)
+            e = m.rayleigh_ritz(X, prec=prec)
+        ev[prec] = e.cpu().numpy()
+        del X
+        torch.cuda.empty_cache()
+    err32 = np.max(np.abs(ev[fe.FE_F32][:k] - ev[fe.FE_F64][:k]))
+    errbf = np.max(np.abs(ev[fe.FE_BF16_F32ACC][:k] - ev[fe.FE_F64][:k]))
+    print(f"p = 5 slab, lowest {k} Ritz values vs FP64: float {err32:.3e}, bf16 {errbf:.3e} Ha")
+    assert err32 <= 1e-5
+    assert errbf <= 1e-2
 
 
 def test_large_lcpd_slab_poisson_and_blocked_filter(fe):
@@ -134,4 +181,36 @@ def test_large_lcpd_slab_poisson_and_blocked_filter(fe):
     ref = assembly.apply_H_rows(om, V, X0, rows, Ke=Ke, M=M)
     got = Y[torch.tensor(rows, device="cuda"), 256:512].double().cpu().numpy()
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-5
+    mag = assembly.apply_H_rows(om, np.abs(V), np.abs(X0), rows, Ke=np.abs(Ke), M=M)
+    assert_operator_entries(got, ref, mag, 1e-6, "large slab rows")
     assert torch.all(Y[:, :256] == 0) and torch.all(Y[:, 512:] == 0)
+    del Y
+    torch.cuda.empty_cache()
+
+    # one full CheFSI cycle of the configuration: the 1024-wide array filtered in four
+    # 256-vector blocks at degree 40, then Rayleigh-Ritz over all 1024 vectors
+    m.set_rr_products(True)
+    lo, hi = m.lanczos_bounds(torch.tensor(W.lanczos_start(m.n_psi), device="cuda"), 20)
+    a = lo + R_FILTER * (hi - lo)
+    for blk in range(4):
+        Xall[:, 256 * blk:256 * (blk + 1)].copy_(
+            torch.from_numpy(W.start_block(slab, nvec=256, seed=2005 + blk)))
+        m.cheb_filter(Xall[:, 256 * blk:256 * (blk + 1)], slab.degree, a, hi, lo,
+                      prec=fe.FE_F32)
+    theta = m.rayleigh_ritz(Xall, prec=fe.FE_F32).cpu().numpy()
+    # ascending, and inside the Lanczos upper bound of the spectrum (the smallest Lanczos
+    # Ritz value bounds the lowest eigenvalue from above, so it bounds nothing here)
+    assert np.all(np.diff(theta) >= 0) and theta[-1] <= hi
+    # what Rayleigh-Ritz guarantees at any size, on sampled columns (block edges included):
+    # X^T X = I and X^T Ht X = diag(theta), in double from the float block
+    cols = np.unique(np.concatenate([[0, 255, 256, 511, 512, 767, 768, 1023],
+                                     rng.choice(1024, 24, replace=False)]))
+    ct = torch.tensor(cols, device="cuda")
+    Xs = Xall[:, ct].contiguous()
+    HXs = m.apply_H(Xs, prec=fe.FE_F32)
+    Xd = Xs.double()
+    G = (Xd.T @ Xd).cpu().numpy()
+    Hs = (Xd.T @ HXs.double()).cpu().numpy()
+    assert np.max(np.abs(G - np.eye(len(cols)))) <= 1e-4
+    scale = max(1.0, float(np.max(np.abs(theta))))
+    assert np.max(np.abs(Hs - np.diag(theta[cols]))) <= 1e-4 * scale

@@ -4,12 +4,19 @@ Rayleigh-Ritz against the FP64 CPU oracle (called through the C ABI).
 Tolerances: FP64 H X <= 1e-10 relative (Frobenius); FP32 H X <= 2e-5 relative (float
 rounding of ~50 accumulated products per entry, u = 6e-8, with margin); FP64 Ritz values
 <= 1e-8 Ha against the oracle's Householder-QR + dense eigh.
+
+Every operator result is also bounded entry by entry (tests/entrywise.py): |Y - Y_ref|_Iv
+<= tol (|Ht| |X|)_Iv, the floating-point bound of a sum of products, with tol = 1e-13 for
+FP64 (~900 u) and 1e-6 for FP32 (~17 u); filter results column by column against the
+column's largest entry (1e-11 FP64, 1e-5 FP32).  A seam plane or tile face wrong by far
+less than the Frobenius bounds allow fails these.
 """
 import numpy as np
 import pytest
 import torch
 
 import workloads as W
+from entrywise import assert_column_maxabs, assert_operator_entries, magnitude
 from oracle import assembly, chefsi
 from oracle.mesh import Mesh as OMesh
 
@@ -65,6 +72,7 @@ def test_apply_H_f64_matches_oracle(fe, L, ncell, p, dirichlet, nvec, ld):
     Y = ybuf[:, :nvec].cpu().numpy()
     ref = H @ X
     assert np.linalg.norm(Y - ref) / np.linalg.norm(ref) <= 1e-10
+    assert_operator_entries(Y, ref, magnitude(H, X), 1e-13, "FP64 H X")
     # padding columns beyond nvec are untouched
     if ld > nvec:
         assert torch.all(ybuf[:, nvec:] == 7.0)
@@ -87,6 +95,7 @@ def test_apply_H_f32_matches_oracle(fe, L, ncell, p, dirichlet, nvec, ld):
     ref = H @ X.astype(np.float64)
     Y = ybuf[:, :nvec].double().cpu().numpy()
     assert np.linalg.norm(Y - ref) / np.linalg.norm(ref) <= 2e-5
+    assert_operator_entries(Y, ref, magnitude(H, X), 1e-6, "FP32 H X")
 
 
 def test_apply_H_is_deterministic(fe):
@@ -120,6 +129,7 @@ def test_cheb_filter_matches_oracle(fe, prec, tol):
         m.cheb_filter(Xg, degree, a, hi, lo, prec=p_)
         got = Xg.double().cpu().numpy()
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
+        assert_column_maxabs(got, ref, 1e-11 if prec == "f64" else 1e-5, f"degree {degree}")
 
 
 def test_lanczos_bounds_match_oracle(fe):

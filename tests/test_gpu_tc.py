@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 import torch
 
+from entrywise import assert_operator_entries, magnitude
 from oracle import assembly
 from oracle.mesh import Mesh as OMesh
 
@@ -52,6 +53,10 @@ def test_apply_H_bf16_matches_oracle(fe, L, ncell, p, dirichlet, nvec, ld):
         fe._lib.call("fe_apply_H", m.handle, fe._ptr(buf), fe._ptr(y), nvec, ld, prec)
         got = y[:, :nvec].double().cpu().numpy()
         errs[prec] = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        # entry bound: both bf16 operands rounded (2^-8 relative each) -> 2e-2 of the terms'
+        # magnitudes; FP32 as in the FP32 operator tests
+        assert_operator_entries(got, ref, magnitude(H, X), 2e-2 if prec == fe.FE_BF16_F32ACC
+                                else 1e-6, f"precision {prec}")
         if ld > nvec:
             assert torch.all(y[:, nvec:] == 3.0)
     assert errs[fe.FE_BF16_F32ACC] <= 1e-2, errs
