@@ -176,6 +176,15 @@ class Mesh:
         call("fe_apply_H", self._h, _ptr(X), _ptr(Y), nvec, X.stride(0), int(prec))
         return Y
 
+    def potential_vjp(self, X, Ybar, prec=FE_F64):
+        """dL/dV_eff = sum_v Ybar_Iv X_Iv for Y = Ht X (fe_potential_vjp)."""
+        assert X.dtype == Ybar.dtype == self._block_dtype(prec)
+        assert X.shape == Ybar.shape and X.stride(0) == Ybar.stride(0) and X.shape[0] == self.n_psi
+        g = self._f64(self.n_psi)
+        call("fe_potential_vjp", self._h, _ptr(X), _ptr(Ybar), X.shape[1], X.stride(0), _ptr(g),
+             int(prec))
+        return g
+
     def cheb_filter(self, X, degree, a, b, a0, prec=FE_F64):
         assert X.dtype == self._block_dtype(prec) and X.shape[0] == self.n_psi
         call("fe_cheb_filter", self._h, _ptr(X), X.shape[1], X.stride(0), int(degree), float(a),

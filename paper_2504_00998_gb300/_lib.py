@@ -35,6 +35,7 @@ EXPORTS = [
     "fe_batch_rayleigh_ritz", "fe_density", "fe_occupations", "fe_mixer_create",
     "fe_mixer_destroy", "fe_mixer_step", "fe_lda_exchange", "fe_planar", "fe_dipole", "fe_vbare_phi",
     "fe_set_nonlocal", "fe_set_kpoint", "fe_set_potential_quad", "fe_interp_quad",
+    "fe_potential_vjp",
 ]
 
 
@@ -83,6 +84,7 @@ def load(path=LIB_PATH):
         "fe_set_atoms": ([P, I, P, P, D, D, D], I),
         "fe_set_potential": ([P, P], I),
         "fe_apply_H": ([P, P, P, I64, I64, I], I),
+        "fe_potential_vjp": ([P, P, P, I64, I64, P, I], I),
         "fe_cheb_filter": ([P, P, I64, I64, I, D, D, D, I], I),
         "fe_cheb_filter_static": ([P, P, I64, I64, I, D, D, D, I], I),
         "fe_poisson_solve": ([P, P, C.POINTER(FePoissonBC), P, P, C.POINTER(FeSolveInfo)], I),

@@ -4,6 +4,10 @@
   (Eq. governing_equations CEF / APD).  Backward is the adjoint solve: K is symmetric, so
   dL/df = solve(dL/dphi, phi_c = 0) on the free nodes and
   dL/dphi_c = (dL/dphi)_c - (K lambda)_c on the constrained nodes.
+* ``HamiltonianApply``: Y = Ht(V_eff) X (Eq. Veff and Hloc).  Ht is symmetric (Hermitian
+  for a Bloch wave vector), so dL/dX = Ht Ybar (one more fe_apply_H); V_eff enters only
+  through diag(V_eff), so dL/dV_eff = sum_v Ybar_Iv X_Iv (fe_potential_vjp; for complex
+  blocks the real part of Ybar conj(X), the sum over the (re, im) lanes).
 * ``SlabEnergy``: E(R, field, dV) of the slab (Eq. electrostatics Energy with the local
   pseudopotential and V_app terms).  The potential maximises E over the free nodes, so the
   gradient needs no adjoint solve (envelope theorem); the position gradient is the
@@ -15,7 +19,7 @@ import dataclasses
 
 import torch
 
-from . import FE_BIAS_CEF, Mesh
+from . import FE_BIAS_CEF, FE_F64, Mesh
 
 
 class PoissonSolve(torch.autograd.Function):
@@ -43,6 +47,36 @@ class PoissonSolve(torch.autograd.Function):
             klam = mesh.poisson_apply_K(grad_f)
             grad_phic = torch.where(mask, g - klam, zero)
         return grad_f, grad_phic, None, None, None
+
+
+class HamiltonianApply(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, V, mesh, prec):
+        X = X.detach().contiguous()
+        V = V.detach().contiguous()
+        mesh.set_potential(V)
+        Y = mesh.apply_H(X, prec=prec)
+        ctx.save_for_backward(X, V)
+        ctx.mesh, ctx.prec = mesh, prec
+        return Y
+
+    @staticmethod
+    def backward(ctx, gY):
+        X, V = ctx.saved_tensors
+        mesh, prec = ctx.mesh, ctx.prec
+        gY = gY.contiguous().to(X.dtype)
+        gX = gV = None
+        mesh.set_potential(V)   # the operator of the forward pass
+        if ctx.needs_input_grad[0]:
+            gX = mesh.apply_H(gY, prec=prec)
+        if ctx.needs_input_grad[1]:
+            gV = mesh.potential_vjp(X, gY, prec=prec)
+        return gX, gV, None, None
+
+
+def apply_H(mesh, X, V, prec=FE_F64):
+    """Y = Ht(V) X, differentiable in X and in the collocated potential V (float64 [n_psi])."""
+    return HamiltonianApply.apply(X, V, mesh, prec)
 
 
 class SlabEnergy(torch.autograd.Function):

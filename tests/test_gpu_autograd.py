@@ -164,3 +164,85 @@ def test_poisson_adjoint_matches_finite_differences(fe, ag, kind):
         fd = (Lof(f0, phic.detach() + h * dc) - Lof(f0, phic.detach() - h * dc)) / (2 * h)
         an = float(torch.sum(grads[1] * dc))
         assert abs(an - fd) <= 1e-6 * abs(fd), (an, fd)
+
+
+def _hx_loss(ag, m, X, V, W, prec):
+    Y = ag.apply_H(m, X, V, prec)
+    # quadratic in Y so that Ybar = W + Y depends on the forward result
+    return (W.conj() * Y).real.sum() + 0.5 * (Y.abs() ** 2).sum()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_hamiltonian_autograd(fe, ag, prec):
+    """dL/dX = Ht Ybar and dL/dV = sum_v Ybar X through the adjoint kernels, against the
+    oracle's assembled Ht and central finite differences (step 1e-4) along random
+    directions; the loss is quadratic in (X, V) direction by direction, so the difference
+    quotient carries round-off only."""
+    p_ = fe.FE_F64 if prec == "f64" else fe.FE_F32
+    dt = torch.float64 if prec == "f64" else torch.float32
+    L, nc, p = (4.0, 4.0, 9.0), (2, 2, 4), 3
+    om = OMesh(L, nc, p)
+    m = fe.Mesh(L, nc, p)
+    rng = np.random.default_rng(51)
+    Vn = rng.uniform(-1.0, 1.0, om.n_psi)
+    Xn = rng.standard_normal((om.n_psi, 8)).astype(np.float32).astype(np.float64)
+    Wn = rng.standard_normal((om.n_psi, 8))
+    V = torch.tensor(Vn, device="cuda", requires_grad=True)
+    X = torch.tensor(Xn, dtype=dt, device="cuda", requires_grad=True)
+    W = torch.tensor(Wn, dtype=dt, device="cuda")
+    _hx_loss(ag, m, X, V, W, p_).backward()
+    H = assembly.hamiltonian(om, Vn)
+    Ybar = Wn + H @ Xn
+    gX_ref, gV_ref = H @ Ybar, np.sum(Ybar * Xn, axis=1)
+    tol = 1e-10 if prec == "f64" else 2e-5
+    gX, gV = X.grad.double().cpu().numpy(), V.grad.cpu().numpy()
+    assert np.linalg.norm(gX - gX_ref) / np.linalg.norm(gX_ref) <= tol
+    assert np.linalg.norm(gV - gV_ref) / np.linalg.norm(gV_ref) <= tol
+    if prec == "f64":
+        with torch.no_grad():
+            for _ in range(2):
+                dV = torch.tensor(rng.standard_normal(om.n_psi), device="cuda")
+                dX = torch.tensor(rng.standard_normal(Xn.shape), device="cuda")
+                fd_v = (_hx_loss(ag, m, X, V + H_FD * dV, W, p_)
+                        - _hx_loss(ag, m, X, V - H_FD * dV, W, p_)).item() / (2 * H_FD)
+                fd_x = (_hx_loss(ag, m, X + H_FD * dX, V, W, p_)
+                        - _hx_loss(ag, m, X - H_FD * dX, V, W, p_)).item() / (2 * H_FD)
+                an_v = float((V.grad * dV).sum())
+                an_x = float((X.grad * dX).sum())
+                assert abs(fd_v - an_v) <= 1e-6 * abs(an_v)
+                assert abs(fd_x - an_x) <= 1e-6 * abs(an_x)
+
+
+def test_hamiltonian_autograd_bloch(fe, ag):
+    """Complex blocks at a Bloch wave vector: dL/dX = Ht_k Ybar (Hermitian) and
+    dL/dV = Re sum_v Ybar conj(X), checked by central differences along real V and complex
+    X directions (PyTorch's convention: dL = Re sum conj(grad) dX)."""
+    L, nc, p = (4.0, 4.0, 9.0), (2, 2, 4), 3
+    m = fe.Mesh(L, nc, p)
+    m.set_kpoint(0.3, -0.2)
+    n = m.n_psi
+    rng = np.random.default_rng(52)
+    V = torch.tensor(rng.uniform(-1.0, 1.0, n), device="cuda", requires_grad=True)
+    Xc = rng.standard_normal((n, 4)) + 1j * rng.standard_normal((n, 4))
+    X = torch.tensor(Xc, dtype=torch.complex128, device="cuda", requires_grad=True)
+    W = torch.tensor(rng.standard_normal((n, 4)) + 1j * rng.standard_normal((n, 4)),
+                     dtype=torch.complex128, device="cuda")
+    _hx_loss(ag, m, X, V, W, fe.FE_F64).backward()
+    with torch.no_grad():
+        dV = torch.tensor(rng.standard_normal(n), device="cuda")
+        dX = torch.tensor(rng.standard_normal((n, 4)) + 1j * rng.standard_normal((n, 4)),
+                          dtype=torch.complex128, device="cuda")
+        fd_v = (_hx_loss(ag, m, X, V + H_FD * dV, W, fe.FE_F64)
+                - _hx_loss(ag, m, X, V - H_FD * dV, W, fe.FE_F64)).item() / (2 * H_FD)
+        fd_x = (_hx_loss(ag, m, X + H_FD * dX, V, W, fe.FE_F64)
+                - _hx_loss(ag, m, X - H_FD * dX, V, W, fe.FE_F64)).item() / (2 * H_FD)
+        an_v = float((V.grad * dV).sum())
+        an_x = float((X.grad.conj() * dX).real.sum())
+    assert abs(fd_v - an_v) <= 1e-6 * abs(an_v)
+    assert abs(fd_x - an_x) <= 1e-6 * abs(an_x)
+    with pytest.raises(fe.FeError):   # the adjoint covers the collocated potential only
+        mq = fe.Mesh(L, nc, p)
+        mq.set_potential_quad(torch.zeros(mq.n_cells * (p + 1) ** 3, dtype=torch.float64,
+                                          device="cuda"))
+        Xq = torch.zeros((mq.n_psi, 2), dtype=torch.float64, device="cuda")
+        mq.potential_vjp(Xq, Xq)
