@@ -7,8 +7,23 @@
 // instance keeps its own geometry, potential, block pointers and recurrence coefficients
 // (alpha, beta, shift), read from a device array of per-instance descriptors.  The shared
 // element coefficient table requires a common p and cell size.
+//
+// Launch configuration (autotuned): the work of one batched launch is the set of (instance,
+// xy block, vector tile, z segment) items.  Two of its parameters decide how that work maps
+// onto the GPU and are chosen per batch by timing: the z-segment length (cell layers per
+// item: short segments give more, smaller items and better balance across slabs of uneven
+// height, long ones amortise the halo planes each segment re-reads) and the grid form (one
+// CTA per item, or a persistent grid of resident CTAs that take items from a device
+// counter as they finish).  On the first batched operator call every candidate runs one
+// operator launch on the batch's own blocks (into the filter's scratch block) and the
+// fastest is kept; the choice is cached for the process per device, precision and batch
+// shape, so later batches of the same shape skip the timing.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "fe_internal.h"
@@ -23,6 +38,13 @@ struct fe_batch {
   void* d_rr = nullptr;     // n x n work of the batched Rayleigh-Ritz
   size_t rr_bytes = 0;
   std::vector<char> h_rr;   // host work of the batched eigensolver
+  // launch configuration: z-segment length (0: occupancy heuristic), persistent grid
+  int zseg = 0;
+  int persistent = 0;
+  bool configured = false;  // chosen by the tuner, taken from the cache, or set by the caller
+  double tuned_ms = 0.0;    // the chosen candidate's launch time when timed here
+  int ncand = 0;            // candidates timed for this batch (0: cache or caller)
+  unsigned long long* d_counter = nullptr;   // work counter of the persistent grid
 };
 
 namespace {
@@ -89,21 +111,48 @@ void fill_io(const fe_batch* b, KronInst<T>* inst, const void* const* X, void* c
 }
 
 template <typename T>
-int64_t plan(const fe_batch* b, KronInst<T>* inst) {
+int64_t plan_with(const fe_batch* b, KronInst<T>* inst, int zseg) {
   const int n = (int)b->meshes.size();
   for (int i = 0; i < n; ++i) inst[i].g = fe_geom(b->meshes[i], true);
-  if constexpr (sizeof(T) == 8) return fe::kron_batch_plan_f64(b->p, inst, n);
-  else return fe::kron_batch_plan_f32(b->p, inst, n);
+  if constexpr (sizeof(T) == 8) return fe::kron_batch_plan_f64(b->p, inst, n, zseg);
+  else return fe::kron_batch_plan_f32(b->p, inst, n, zseg);
 }
 
 template <typename T>
-fe_status launch(const fe_batch* b, const KronInst<T>* d_inst, int64_t total, bool use_z,
-                 bool full) {
+int64_t plan(const fe_batch* b, KronInst<T>* inst) {
+  return plan_with(b, inst, b->zseg);
+}
+
+fe_status ensure_counter(fe_batch* b) {
+  if (b->d_counter) return FE_OK;
+  if (cudaMalloc((void**)&b->d_counter, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    b->d_counter = nullptr;
+    return fe_fail(FE_ENOMEM, "batch work counter could not be allocated");
+  }
+  return FE_OK;
+}
+
+template <typename T>
+fe_status launch_with(fe_batch* b, const KronInst<T>* d_inst, int64_t total, bool use_z,
+                      bool full, int persistent) {
   const int n = (int)b->meshes.size();
+  unsigned long long* counter = nullptr;
+  if (persistent) {
+    FE_TRY(ensure_counter(b));
+    counter = b->d_counter;
+  }
   if constexpr (sizeof(T) == 8)
-    return fe::kron_batch_f64(b->meshes[0]->coefH, b->p, d_inst, n, total, use_z, full, b->stream);
+    return fe::kron_batch_f64(b->meshes[0]->coefH, b->p, d_inst, n, total, use_z, full, b->stream,
+                              counter);
   else
-    return fe::kron_batch_f32(b->meshes[0]->coefH, b->p, d_inst, n, total, use_z, full, b->stream);
+    return fe::kron_batch_f32(b->meshes[0]->coefH, b->p, d_inst, n, total, use_z, full, b->stream,
+                              counter);
+}
+
+template <typename T>
+fe_status launch(fe_batch* b, const KronInst<T>* d_inst, int64_t total, bool use_z, bool full) {
+  return launch_with(b, d_inst, total, use_z, full, b->persistent);
 }
 
 template <typename T>
@@ -113,10 +162,107 @@ bool all_full(const KronInst<T>* inst, size_t n) {
   return true;
 }
 
+// ---- autotuner --------------------------------------------------------------------------------
+std::mutex g_tune_mutex;
+std::map<std::string, std::pair<int, int>> g_tune_cache;   // shape key -> (zseg, persistent)
+
+std::string tune_key(const fe_batch* b, int eb, const int64_t* nvec) {
+  std::string k = std::to_string(b->device) + "|" + std::to_string(b->p) + "|" +
+                  std::to_string(eb);
+  for (size_t i = 0; i < b->meshes.size(); ++i) {
+    const fe_mesh* m = b->meshes[i];
+    k += "|" + std::to_string(m->nx) + "," + std::to_string(m->ny) + "," +
+         std::to_string(m->nz) + "," + std::to_string(m->NZs) + "," + std::to_string(nvec[i]);
+  }
+  return k;
+}
+
+// Time every candidate launch configuration on the batch's blocks (X -> the instances'
+// filter scratch blocks W, which the caller owns for the duration) and keep the fastest.
+template <typename T>
+fe_status tune(fe_batch* b, const void* const* X, void* const* W, const int64_t* nvec,
+               const int64_t* ld) {
+  if (b->configured) return FE_OK;
+  const std::string key = tune_key(b, (int)sizeof(T), nvec);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      b->zseg = it->second.first;
+      b->persistent = it->second.second;
+      b->configured = true;
+      b->ncand = 0;
+      return FE_OK;
+    }
+  }
+  const size_t n = b->meshes.size();
+  std::vector<KronInst<T>> inst(n);
+  std::vector<double> one(n, 1.0), zero(n, 0.0);
+  cudaEvent_t e0, e1;
+  FE_CUDA(cudaEventCreate(&e0));
+  FE_CUDA(cudaEventCreate(&e1));
+  double best = 1e300;
+  int best_z = 0, best_p = 0, tried = 0;
+  std::vector<int> resolved;
+  fe_status st = FE_OK;
+  for (int zreq : {0, 2, 4, 8, 16, 1 << 30}) {
+    for (size_t i = 0; i < n; ++i) inst[i].io.nvec = nvec[i];
+    const int64_t total = plan_with(b, inst.data(), zreq);
+    const int zres = inst[0].g.zseg;
+    if (std::find(resolved.begin(), resolved.end(), zres) != resolved.end()) continue;
+    resolved.push_back(zres);
+    fill_io(b, inst.data(), X, W, nullptr, nvec, ld, one.data(), zero.data(), zero.data());
+    st = grow_desc(b, n * sizeof(KronInst<T>));
+    if (st != FE_OK) break;
+    if (cudaMemcpyAsync(b->d_desc, inst.data(), n * sizeof(KronInst<T>), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess) {
+      cudaGetLastError();
+      st = fe_fail(FE_ECUDA, "batch tuner: descriptor upload failed");
+      break;
+    }
+    const bool full = all_full(inst.data(), n);
+    for (int pers = 0; pers <= 1 && st == FE_OK; ++pers) {
+      const KronInst<T>* d = (const KronInst<T>*)b->d_desc;
+      st = launch_with(b, d, total, false, full, pers);   // warm-up
+      if (st != FE_OK) break;
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < 2 && st == FE_OK; ++r) st = launch_with(b, d, total, false, full, pers);
+      cudaEventRecord(e1, b->stream);
+      if (st != FE_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaGetLastError();
+        st = fe_fail(FE_ECUDA, "batch tuner: timing failed");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ++tried;
+      if (ms / 2.0 < best) {
+        best = ms / 2.0;
+        best_z = zreq == 0 ? 0 : zres;
+        best_p = pers;
+      }
+    }
+    if (st != FE_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FE_TRY(st);
+  b->zseg = best_z;
+  b->persistent = best_p;
+  b->tuned_ms = best;
+  b->ncand = tried;
+  b->configured = true;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = {best_z, best_p};
+  return FE_OK;
+}
+
 template <typename T>
 fe_status batch_apply(fe_batch* b, const void* const* X, void* const* Y, const int64_t* nvec,
                       const int64_t* ld) {
   const size_t n = b->meshes.size();
+  FE_TRY(tune<T>(b, X, Y, nvec, ld));
   std::vector<KronInst<T>> inst(n);
   std::vector<double> one(n, 1.0), zero(n, 0.0);
   for (size_t i = 0; i < n; ++i) inst[i].io.nvec = nvec[i];
@@ -138,6 +284,7 @@ fe_status batch_filter(fe_batch* b, void* const* X, const int64_t* nvec, const i
   std::vector<void*> W(n);
   for (size_t i = 0; i < n; ++i)
     FE_TRY(fe_ws(b->meshes[i], WS_CHEB, (size_t)b->meshes[i]->n_psi * ld[i] * eb, &W[i]));
+  FE_TRY(tune<T>(b, (const void* const*)X, W.data(), nvec, ld));
   std::vector<KronInst<T>> inst((size_t)degree * n);
   for (size_t i = 0; i < n; ++i) inst[i].io.nvec = nvec[i];
   const int64_t total = plan(b, inst.data());
@@ -220,16 +367,41 @@ extern "C" fe_status fe_batch_create(fe_mesh* const* meshes, int n, fe_batch** o
 extern "C" fe_status fe_batch_destroy(fe_batch* b) {
   if (!b) return FE_OK;
   fe_status st = FE_OK;
-  if (b->d_desc || b->d_rr) {
+  if (b->d_desc || b->d_rr || b->d_counter) {
     if (cudaSetDevice(b->device) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess ||
         (b->d_desc && cudaFree(b->d_desc) != cudaSuccess) ||
-        (b->d_rr && cudaFree(b->d_rr) != cudaSuccess)) {
+        (b->d_rr && cudaFree(b->d_rr) != cudaSuccess) ||
+        (b->d_counter && cudaFree(b->d_counter) != cudaSuccess)) {
       cudaGetLastError();
       st = fe_fail(FE_ECUDA, "fe_batch_destroy: could not release the batch work arrays");
     }
   }
   delete b;
   return st;
+}
+
+extern "C" fe_status fe_batch_tuning(const fe_batch* b, int* zseg, int* persistent,
+                                     double* best_ms, int* ncand) {
+  if (!b || !zseg || !persistent || !best_ms || !ncand)
+    return fe_fail(FE_EINVAL, "fe_batch_tuning: null argument");
+  *zseg = b->zseg;
+  *persistent = b->persistent;
+  *best_ms = b->tuned_ms;
+  *ncand = b->ncand;
+  return b->configured ? FE_OK
+                       : fe_fail(FE_EINVAL, "fe_batch_tuning: no batched operator call yet");
+}
+
+extern "C" fe_status fe_batch_set_launch(fe_batch* b, int zseg, int persistent) {
+  if (!b) return fe_fail(FE_EINVAL, "fe_batch_set_launch: null batch");
+  if (zseg < 0 || (persistent != 0 && persistent != 1))
+    return fe_fail(FE_EINVAL, "fe_batch_set_launch: need zseg >= 0 and persistent 0 or 1");
+  b->zseg = zseg;
+  b->persistent = persistent;
+  b->configured = true;
+  b->tuned_ms = 0.0;
+  b->ncand = 0;
+  return FE_OK;
 }
 
 extern "C" fe_status fe_batch_apply_H(fe_batch* b, const void* const* X, void* const* Y,

@@ -27,6 +27,7 @@
 // memory) so that several share an SM and one CTA's barriers overlap another's work.
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -645,6 +646,36 @@ kron_batch_kernel(const KronCoefT<T> cf, const KronInst<T>* __restrict__ inst, i
   kron_body<T, CH, TL, FULL, CT>(cf, g, io, (int)(r % nxy), (int)(local % nvt), (int)(r / nxy));
 }
 
+// Persistent batched form: a grid of resident CTAs takes the batch's work items (the CTAs of
+// the one-CTA-per-item grid above) from a device counter, so that the items of tall and
+// short instances spread over the SMs as they finish (dynamic load balance for uneven slab
+// heights).  The counter starts at zero for each launch.
+template <typename T, int CH, class TL, bool FULL, bool CT>
+__global__ void __launch_bounds__(TL::NTHR, (KronMinBlocks<T, CH, TL>::value))
+kron_batch_persist_kernel(const KronCoefT<T> cf, const KronInst<T>* __restrict__ inst, int ninst,
+                          int64_t total, unsigned long long* __restrict__ counter) {
+  __shared__ long long s_item;
+  for (;;) {
+    __syncthreads();   // every thread is done with the previous item's shared memory
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t b = s_item;
+    if (b >= total) break;
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (inst[mid].cta0 <= b) lo = mid; else hi = mid - 1;
+    }
+    const KronGeom g = inst[lo].g;
+    const KronIO<T> io = inst[lo].io;
+    const int64_t local = b - inst[lo].cta0;
+    const int nxy = g.nbx * g.nby;
+    const int64_t nvt = inst[lo].nvt;
+    const int64_t r = local / nvt;
+    kron_body<T, CH, TL, FULL, CT>(cf, g, io, (int)(r % nxy), (int)(local % nvt), (int)(r / nxy));
+  }
+}
+
 // Dynamic shared memory limit, and the largest shared-memory carveout so that the residency
 // of these kernels is set by registers and their own shared memory, not by the L1 split.
 template <typename K>
@@ -750,9 +781,9 @@ fe_status kron_go(const KronCoef& cf, KronGeom g, const KronIO<T>& io, cudaStrea
 }
 
 // batched plan: every instance gets tile TL; z segments are split (uniformly) only while the
-// whole batch has fewer than four CTAs per SM
+// whole batch has fewer than four CTAs per SM, or have the requested length zseg_req > 0
 template <typename T, int CH, class TL>
-int64_t kron_batch_plan_t(KronInst<T>* inst, int n) {
+int64_t kron_batch_plan_t(KronInst<T>* inst, int n, int zseg_req) {
   int nzmax = 1;
   for (int i = 0; i < n; ++i) {
     KronGeom& g = inst[i].g;
@@ -775,7 +806,9 @@ int64_t kron_batch_plan_t(KronInst<T>* inst, int n) {
     return t;
   };
   int zseg = nzmax;
-  while (zseg > 2 && total_for(zseg) < want) zseg = (zseg + 1) / 2;
+  if (zseg_req > 0) zseg = zseg_req < nzmax ? zseg_req : nzmax;
+  else
+    while (zseg > 2 && total_for(zseg) < want) zseg = (zseg + 1) / 2;
   int64_t cta = 0;
   for (int i = 0; i < n; ++i) {
     KronGeom& g = inst[i].g;
@@ -788,44 +821,69 @@ int64_t kron_batch_plan_t(KronInst<T>* inst, int n) {
 
 template <typename T, int CH, class TL>
 fe_status kron_batch_launch_t(const KronCoef& cf, const KronInst<T>* d_inst, int n,
-                              int64_t total, bool use_z, bool full, cudaStream_t st) {
+                              int64_t total, bool use_z, bool full, cudaStream_t st,
+                              unsigned long long* counter) {
   const size_t smem = kron_smem<T, CH, TL>(use_z, true);
   if (smem > 227 * 1024) return fe_fail(FE_EINVAL, "tile needs %zu bytes of shared memory", smem);
   if (total < 1 || total > 0x7fffffffLL) return fe_fail(FE_EINVAL, "batched grid of %lld CTAs", (long long)total);
-  auto kern = full ? kron_batch_kernel<T, CH, TL, true, false> : kron_batch_kernel<T, CH, TL, false, false>;
-  if constexpr (KronShapeTables<T, CH>::value) {
-    if (cf.mass_scale && !cf.cplx)
-      kern = full ? kron_batch_kernel<T, CH, TL, true, true> : kron_batch_kernel<T, CH, TL, false, true>;
-  }
-  FE_TRY(kron_func_setup(kern, smem));
+  const bool ct = KronShapeTables<T, CH>::value && cf.mass_scale && !cf.cplx;
   KronCoefT<T> cft = convert_coef<T>(cf);
-  kern<<<(unsigned)total, TL::NTHR, smem, st>>>(cft, d_inst, n); fe_count_launch();
+  if (counter) {
+    // persistent grid: as many CTAs as stay resident, each taking items from the counter
+    auto kern = full ? kron_batch_persist_kernel<T, CH, TL, true, false>
+                     : kron_batch_persist_kernel<T, CH, TL, false, false>;
+    if constexpr (KronShapeTables<T, CH>::value) {
+      if (ct) kern = full ? kron_batch_persist_kernel<T, CH, TL, true, true>
+                          : kron_batch_persist_kernel<T, CH, TL, false, true>;
+    }
+    FE_TRY(kron_func_setup(kern, smem));
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TL::NTHR, smem) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    const int64_t grid = std::min<int64_t>(total, (int64_t)per_sm * device_sms());
+    if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st) != cudaSuccess) {
+      cudaGetLastError();
+      return fe_fail(FE_ECUDA, "batched kron: counter reset failed");
+    }
+    kern<<<(unsigned)grid, TL::NTHR, smem, st>>>(cft, d_inst, n, total, counter); fe_count_launch();
+  } else {
+    auto kern = full ? kron_batch_kernel<T, CH, TL, true, false> : kron_batch_kernel<T, CH, TL, false, false>;
+    if constexpr (KronShapeTables<T, CH>::value) {
+      if (ct) kern = full ? kron_batch_kernel<T, CH, TL, true, true> : kron_batch_kernel<T, CH, TL, false, true>;
+    }
+    FE_TRY(kron_func_setup(kern, smem));
+    kern<<<(unsigned)total, TL::NTHR, smem, st>>>(cft, d_inst, n); fe_count_launch();
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fe_fail(FE_ECUDA, "batched kron launch: %s", cudaGetErrorString(e));
   return FE_OK;
 }
 
 template <typename T, int CH, int NCH>
-int64_t kron_batch_plan_dispatch(int p, KronInst<T>* inst, int n) {
+int64_t kron_batch_plan_dispatch(int p, KronInst<T>* inst, int n, int zseg_req) {
   switch (p) {
-    case 1: return kron_batch_plan_t<T, CH, typename KronTileFor<1, NCH, CH>::type>(inst, n);
-    case 2: return kron_batch_plan_t<T, CH, typename KronTileFor<2, NCH, CH>::type>(inst, n);
-    case 3: return kron_batch_plan_t<T, CH, typename KronTileFor<3, NCH, CH>::type>(inst, n);
-    case 4: return kron_batch_plan_t<T, CH, typename KronTileFor<4, NCH, CH>::type>(inst, n);
-    case 5: return kron_batch_plan_t<T, CH, typename KronTileFor<5, NCH, CH>::type>(inst, n);
-    case 6: return kron_batch_plan_t<T, CH, typename KronTileFor<6, NCH, CH>::type>(inst, n);
+    case 1: return kron_batch_plan_t<T, CH, typename KronTileFor<1, NCH, CH>::type>(inst, n, zseg_req);
+    case 2: return kron_batch_plan_t<T, CH, typename KronTileFor<2, NCH, CH>::type>(inst, n, zseg_req);
+    case 3: return kron_batch_plan_t<T, CH, typename KronTileFor<3, NCH, CH>::type>(inst, n, zseg_req);
+    case 4: return kron_batch_plan_t<T, CH, typename KronTileFor<4, NCH, CH>::type>(inst, n, zseg_req);
+    case 5: return kron_batch_plan_t<T, CH, typename KronTileFor<5, NCH, CH>::type>(inst, n, zseg_req);
+    case 6: return kron_batch_plan_t<T, CH, typename KronTileFor<6, NCH, CH>::type>(inst, n, zseg_req);
     default: return -1;
   }
 }
 
 template <typename T, int CH, int NCH>
 fe_status kron_batch_dispatch(const KronCoef& cf, int p, const KronInst<T>* d_inst, int n,
-                              int64_t total, bool use_z, bool full, cudaStream_t st) {
+                              int64_t total, bool use_z, bool full, cudaStream_t st,
+                              unsigned long long* counter) {
   switch (p) {
 #define FE_BCASE(pp)                                                                      \
   case pp:                                                                                \
     return kron_batch_launch_t<T, CH, typename KronTileFor<pp, NCH, CH>::type>(cf, d_inst, n, \
-                                                                          total, use_z, full, st);
+                                                                          total, use_z, full, st, counter);
     FE_BCASE(1) FE_BCASE(2) FE_BCASE(3) FE_BCASE(4) FE_BCASE(5) FE_BCASE(6)
 #undef FE_BCASE
     default: return fe_fail(FE_EUNSUPPORTED, "p = %d", p);

@@ -213,3 +213,42 @@ def test_batch_rayleigh_ritz_needs_tensor_core_products_for_float(fe):
     with pytest.raises(fe.FeError) as e:
         b.rayleigh_ritz([X], prec=fe.FE_F32)
     assert e.value.status == 7
+
+
+def test_batch_launch_configurations_and_tuner(fe):
+    """Every launch configuration the autotuner chooses among (z-segment length x one CTA
+    per item or a persistent, counter-scheduled grid) gives the same filtered blocks bit
+    for bit; the tuner times them on the first call and reports its choice."""
+    inst = _instances(fe, [3, 9, 6, 2, 7], p=4, nx=2, seed=13)
+    rng = np.random.default_rng(14)
+    X0 = [torch.tensor(rng.standard_normal((om.n_psi, 16)), dtype=torch.float32, device="cuda")
+          for om, _, _ in inst]
+    a, b, a0 = [4.0] * 5, [90.0] * 5, [-1.0] * 5
+    outs = []
+    for zseg, pers in ((0, 0), (0, 1), (2, 0), (2, 1), (4, 1), (16, 0)):
+        batch = fe.Batch([m for _, _, m in inst])
+        batch.set_launch(zseg, pers)
+        Xs = [x.clone() for x in X0]
+        batch.cheb_filter(Xs, 5, a, b, a0, prec=fe.FE_F32)
+        torch.cuda.synchronize()
+        assert batch.tuning()[:2] == (zseg, pers)
+        outs.append(Xs)
+        batch.close()
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):
+            assert torch.equal(x, y)
+    batch = fe.Batch([m for _, _, m in inst])
+    with pytest.raises(fe.FeError):
+        batch.tuning()                      # nothing chosen before the first call
+    Xs = [x.clone() for x in X0]
+    batch.cheb_filter(Xs, 5, a, b, a0, prec=fe.FE_F32)
+    zseg, pers, ms, nc = batch.tuning()
+    assert zseg >= 0 and pers in (0, 1) and ms > 0 and nc >= 4
+    for x, y in zip(outs[0], Xs):
+        assert torch.equal(x, y)
+    batch.close()
+    # a second batch of the same shape takes the cached choice without timing
+    batch = fe.Batch([m for _, _, m in inst])
+    batch.cheb_filter([x.clone() for x in X0], 5, a, b, a0, prec=fe.FE_F32)
+    assert batch.tuning()[:2] == (zseg, pers) and batch.tuning()[3] == 0
+    batch.close()
