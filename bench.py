@@ -41,7 +41,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--prec", choices=["f32", "f64", "bf16"], default="f32")
+    ap.add_argument("--prec", choices=["f32", "f64", "bf16", "f32tc"], default="f32",
+                    help="filter operator: f32 (CUDA cores), f64, bf16 (dense cell matrix on "
+                         "the tensor cores), f32tc (sum-factorised, split-TF32 in-plane "
+                         "contractions on the tensor cores, FP32-accurate)")
     ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep", "p5nl", "scf", "p5k",
                                            "p5q", "p5qs"],
                     default="p5",
@@ -523,8 +526,9 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prec = {"f32": fe.FE_F32, "f64": fe.FE_F64, "bf16": fe.FE_BF16_F32ACC}[args.prec]
-    dtype_name = {"f32": "f32", "f64": "f64", "bf16": "bf16"}[args.prec]
+    prec = {"f32": fe.FE_F32, "f64": fe.FE_F64, "bf16": fe.FE_BF16_F32ACC,
+            "f32tc": fe.FE_F32_F32ACC}[args.prec]
+    dtype_name = {"f32": "f32", "f64": "f64", "bf16": "bf16", "f32tc": "f32 (split tf32)"}[args.prec]
     slab = workload(args.workload)
     nvec, degree = slab.nvec, slab.degree
     lib = fe.load()
@@ -635,7 +639,8 @@ def run_gpu(args):
     launch_ms = phase[2] / degree
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_src = measured_peaks()
-    kernel_key = {fe.FE_F32: "kron_f32_p5", fe.FE_F64: "kron_f64_p5"}.get(prec, "tc_p5")
+    kernel_key = {fe.FE_F32: "kron_f32_p5", fe.FE_F64: "kron_f64_p5",
+                  fe.FE_F32_F32ACC: "ktc_f32_p5"}.get(prec, "tc_p5")
     # (the nonlocal term adds its own kernels to the filter time: no single-kernel traffic)
     traffic = traffic_record(kernel_key) if not nl_desc else None
 

@@ -266,6 +266,25 @@ fe_status fe_batch_cheb_filter(fe_batch* batch, void* const* X, const int64_t* n
 fe_status fe_batch_rayleigh_ritz(fe_batch* batch, void* const* X, int64_t nvec,
                                  const int64_t* ld, double* const* eig, fe_precision prec);
 
+/* Launch configuration of the batched operator, chosen by the library's autotuner (the
+ * paper runs each bias value as its own calculation; batching is this library's).  A
+ * batched launch covers (instance, xy block, vector tile, z segment) work items; on the
+ * first batched operator call of a batch every candidate -- the z-segment length (cell
+ * layers per item: the occupancy heuristic, 2, 4, 8, 16, or each slab's whole height)
+ * crossed with the grid form (one CTA per item, or a persistent grid of resident CTAs
+ * taking items from a device counter, which balances slabs of uneven height) -- runs one
+ * operator launch on the batch's own blocks, and the fastest is kept.  The choice is cached
+ * for the process per device, precision and batch shape (later batches of the same shape
+ * skip the timing).  fe_batch_tuning reports it: *zseg (0: the heuristic's length),
+ * *persistent (0 or 1), *best_ms (the chosen launch's time; 0 when not timed for this
+ * batch), *ncand (candidates timed for this batch; 0 when the choice came from the cache
+ * or from fe_batch_set_launch).  FE_EINVAL before the first batched operator call.
+ * fe_batch_set_launch fixes the configuration instead (zseg >= 0, persistent 0 or 1); the
+ * results do not depend on it. */
+fe_status fe_batch_tuning(const fe_batch* batch, int* zseg, int* persistent, double* best_ms,
+                          int* ncand);
+fe_status fe_batch_set_launch(fe_batch* batch, int zseg, int persistent);
+
 /* ---- analysis outputs (Section 3) ---------------------------------------------------------
  * Per phi plane of a phi-node field f_dev [n_phi], out_dev [NZ] (NZ = nz p + 1 planes, in
  * z order): FE_PLANAR_INTEGRAL gives int_{S_z} f dx dy (Section 3.3's rho0(z)),

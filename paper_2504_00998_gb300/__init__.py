@@ -311,6 +311,16 @@ class Batch:
         call("fe_batch_apply_H", self._h, xp, yp, nvec, ld, int(prec))
         return Ys
 
+    def tuning(self):
+        """(zseg, persistent, best_ms, candidates timed) of the batched launches
+        (fe_batch_tuning)."""
+        z, pers, ms, nc = C.c_int(), C.c_int(), C.c_double(), C.c_int()
+        call("fe_batch_tuning", self._h, C.byref(z), C.byref(pers), C.byref(ms), C.byref(nc))
+        return z.value, pers.value, ms.value, nc.value
+
+    def set_launch(self, zseg, persistent):
+        call("fe_batch_set_launch", self._h, int(zseg), int(persistent))
+
     def cheb_filter(self, Xs, degree, a, b, a0, prec=FE_F64):
         xp, nvec, ld = self._blocks(Xs, prec)
         n = len(Xs)

@@ -35,7 +35,7 @@ EXPORTS = [
     "fe_batch_rayleigh_ritz", "fe_density", "fe_occupations", "fe_mixer_create",
     "fe_mixer_destroy", "fe_mixer_step", "fe_lda_exchange", "fe_planar", "fe_dipole", "fe_vbare_phi",
     "fe_set_nonlocal", "fe_set_kpoint", "fe_set_potential_quad", "fe_interp_quad",
-    "fe_potential_vjp",
+    "fe_potential_vjp", "fe_batch_tuning", "fe_batch_set_launch",
 ]
 
 
@@ -108,6 +108,8 @@ def load(path=LIB_PATH):
         "fe_batch_apply_H": ([P, P, P, P, P, I], I),
         "fe_batch_cheb_filter": ([P, P, P, P, I, P, P, P, I], I),
         "fe_batch_rayleigh_ritz": ([P, P, I64, P, P, I], I),
+        "fe_batch_tuning": ([P, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(I)], I),
+        "fe_batch_set_launch": ([P, I, I], I),
         "fe_density": ([P, P, I64, I64, P, P, I], I),
         "fe_occupations": ([P, I, D, D, P, C.POINTER(D)], I),
         "fe_mixer_create": ([P, I, D, C.POINTER(C.c_void_p)], I),

@@ -35,9 +35,13 @@ bool valid_prec(fe_precision p) {
 
 }  // namespace
 
-// Tensor-core cell-matrix variants live in fe_tc.cu.
+// Tensor-core variants: the dense cell-matrix product (bf16, fe_tc.cu) and the
+// FP32-accurate sum-factorised operator with split-TF32 in-plane contractions
+// (fe_kron_tc.cu).
 fe_status fe_tc_apply(fe_mesh* m, const float* X, float* Y, const float* Z, int64_t nvec,
                       int64_t ld, float alpha, float beta, float shift, fe_precision prec);
+fe_status fe_ktc_apply(fe_mesh* m, const float* X, float* Y, const float* Z, int64_t nvec,
+                       int64_t ld, float alpha, float beta, float shift);
 
 // Y = alpha (Ht - shift) X + beta Z in the requested arithmetic.
 // (plus alpha Ht_nloc X when the mesh carries the nonlocal term)
@@ -80,6 +84,9 @@ fe_status fe_hx_step(fe_mesh* m, const void* X, void* Y, const void* Z, int64_t 
     KronIO<float> io{(const float*)X, ld, (float*)Y, ld, (const float*)Z, ld, m->d_veff_f,
                      nvec, (float)alpha, (float)beta, (float)shift};
     FE_TRY(fe::kron_f32(m->coefH, fe_geom(m, true), io, m->stream));
+  } else if (prec == FE_F32_F32ACC) {
+    FE_TRY(fe_ktc_apply(m, (const float*)X, (float*)Y, (const float*)Z, nvec, ld, (float)alpha,
+                        (float)beta, (float)shift));
   } else {
     FE_TRY(fe_tc_apply(m, (const float*)X, (float*)Y, (const float*)Z, nvec, ld, (float)alpha,
                        (float)beta, (float)shift, prec));

@@ -13,7 +13,7 @@
 
 #define FE_MAXP 6
 #define FE_MAXN1 (FE_MAXP + 1)
-#define FE_NWS 16   // workspace slots of a mesh
+#define FE_NWS 17   // workspace slots of a mesh
 
 // ---- error state ------------------------------------------------------------------------
 fe_status fe_fail(fe_status st, const char* fmt, ...);
@@ -142,12 +142,17 @@ fe_status kron_k1(const KronCoef& cf, const KronGeom& g, const KronIO<double>& i
 // Batched launches: plan fills the tile fields, z segmentation, nvt and cta0 of n host
 // instances (g from fe_geom, io.nvec set) and returns the total CTA count; launch runs one
 // operator application over the device copy of those instances.
-int64_t kron_batch_plan_f64(int p, KronInst<double>* inst, int n);
-int64_t kron_batch_plan_f32(int p, KronInst<float>* inst, int n);
+// zseg_req > 0 asks for that z-segment length (cells per CTA along z); counter != nullptr
+// launches the persistent, dynamically scheduled form (counter: one device word, reset by
+// the launch).
+int64_t kron_batch_plan_f64(int p, KronInst<double>* inst, int n, int zseg_req);
+int64_t kron_batch_plan_f32(int p, KronInst<float>* inst, int n, int zseg_req);
 fe_status kron_batch_f64(const KronCoef& cf, int p, const KronInst<double>* d_inst, int n,
-                         int64_t total_ctas, bool use_z, bool full, cudaStream_t st);
+                         int64_t total_ctas, bool use_z, bool full, cudaStream_t st,
+                         unsigned long long* counter);
 fe_status kron_batch_f32(const KronCoef& cf, int p, const KronInst<float>* d_inst, int n,
-                         int64_t total_ctas, bool use_z, bool full, cudaStream_t st);
+                         int64_t total_ctas, bool use_z, bool full, cudaStream_t st,
+                         unsigned long long* counter);
 }  // namespace fe
 
 // ---- nonlocal projector tables (fe_nonlocal.cu) --------------------------------------------
@@ -231,6 +236,10 @@ struct fe_mesh {
   // tensor-core path: p of the uploaded cell-matrix image, pinned wait-expiry flag
   int tc_img_p = -1;
   int* tc_err_pinned = nullptr;
+  // tensor-core sum-factorised operator (fe_kron_tc.cu): operator images uploaded, and the
+  // host copy of its wait-expiry flag
+  bool ktc_ready = false;
+  int* ktc_err_pinned = nullptr;
 
   cublasHandle_t cublas = nullptr;
   cusolverDnHandle_t cusolver = nullptr;
@@ -239,7 +248,7 @@ struct fe_mesh {
 
 enum { WS_CHEB = 0, WS_RR_X = 1, WS_RR_HX = 2, WS_RR_SMALL = 3, WS_CG = 4, WS_RED = 5,
        WS_LANCZOS = 6, WS_TC = 7, WS_TC_IMG = 8, WS_YCELL = 9, WS_RR_TC32 = 10,
-       WS_PCOARSE = 11, WS_NL = 12, WS_KCELL = 13, WS_XC = 14, WS_KPT = 15 };
+       WS_PCOARSE = 11, WS_NL = 12, WS_KCELL = 13, WS_XC = 14, WS_KPT = 15, WS_KTC = 16 };
 
 fe_status fe_ws(fe_mesh* m, int slot, size_t bytes, void** out);
 // Rayleigh-Ritz of a complex (Bloch) block: nvec, ld count complex entries (fe_kpoint.cu)

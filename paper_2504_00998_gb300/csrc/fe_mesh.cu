@@ -316,6 +316,7 @@ extern "C" fe_status fe_mesh_destroy(fe_mesh* m) {
   fe_nonlocal_free(m);
   fe_quad_free(m);
   if (m->tc_err_pinned) cudaFreeHost(m->tc_err_pinned);
+  if (m->ktc_err_pinned) cudaFreeHost(m->ktc_err_pinned);
   cudaFree(m->d_veff);
   cudaFree(m->d_veff_f);
   cudaFree(m->d_atoms);

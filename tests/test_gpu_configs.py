@@ -94,7 +94,8 @@ def test_p5_slab_sampled_rows(fe):
     ref = assembly.apply_H_rows(om, V, X0, rows, Ke=Ke, M=M)
     # entry bound: the magnitudes of the terms, sum_e |K_e| |S X| and |V| |X|, row by row
     mag = assembly.apply_H_rows(om, np.abs(V), np.abs(X0), rows, Ke=np.abs(Ke), M=M)
-    for prec, tol, etol in ((fe.FE_F64, 1e-10, 1e-13), (fe.FE_F32, 2e-5, 1e-6)):
+    for prec, tol, etol in ((fe.FE_F64, 1e-10, 1e-13), (fe.FE_F32, 2e-5, 1e-6),
+                            (fe.FE_F32_F32ACC, 2e-5, 4e-6)):
         Xg = torch.tensor(X0, dtype=fe.storage_dtype(prec), device="cuda")
         Y = m.apply_H(Xg, prec=prec)
         got = Y[torch.tensor(rows, device="cuda")].double().cpu().numpy()
@@ -120,7 +121,8 @@ def test_p5_slab_mixed_eigenvalues_vs_fp64(fe):
     X0 = torch.from_numpy(W.start_block(slab))
     k = min(int(slab.n_electrons // 2), slab.nvec - 8)
     ev = {}
-    for prec, tc in ((fe.FE_F64, False), (fe.FE_F32, True), (fe.FE_BF16_F32ACC, True)):
+    for prec, tc in ((fe.FE_F64, False), (fe.FE_F32, True), (fe.FE_F32_F32ACC, True),
+                     (fe.FE_BF16_F32ACC, True)):
         m.set_rr_products(tc)
         X = X0.to("cuda", fe.storage_dtype(prec))
         for _ in range(2):
@@ -131,8 +133,10 @@ def test_p5_slab_mixed_eigenvalues_vs_fp64(fe):
         torch.cuda.empty_cache()
     err32 = np.max(np.abs(ev[fe.FE_F32][:k] - ev[fe.FE_F64][:k]))
     errbf = np.max(np.abs(ev[fe.FE_BF16_F32ACC][:k] - ev[fe.FE_F64][:k]))
-    print(f"p = 5 slab, lowest {k} Ritz values vs FP64: float {err32:.3e}, bf16 {errbf:.3e} Ha")
-    assert err32 <= 1e-5
+    errtc = np.max(np.abs(ev[fe.FE_F32_F32ACC][:k] - ev[fe.FE_F64][:k]))
+    print(f"p = 5 slab, lowest {k} Ritz values vs FP64: float {err32:.3e}, split-TF32 "
+          f"tensor cores {errtc:.3e}, bf16 {errbf:.3e} Ha")
+    assert err32 <= 1e-5 and errtc <= 1e-5
     assert errbf <= 1e-2
 
 
@@ -203,8 +207,9 @@ def test_large_lcpd_slab_poisson_and_blocked_filter(fe):
     assert np.all(np.diff(theta) >= 0) and theta[-1] <= hi
     # what Rayleigh-Ritz guarantees at any size, on sampled columns (block edges included):
     # X^T X = I and X^T Ht X = diag(theta), in double from the float block
-    cols = np.unique(np.concatenate([[0, 255, 256, 511, 512, 767, 768, 1023],
-                                     rng.choice(1024, 24, replace=False)]))
+    edges = [0, 255, 256, 511, 512, 767, 768, 1023]
+    rest = np.setdiff1d(np.arange(1024), edges)
+    cols = np.sort(np.concatenate([edges, rng.choice(rest, 24, replace=False)]))   # 32 columns
     ct = torch.tensor(cols, device="cuda")
     Xs = Xall[:, ct].contiguous()
     HXs = m.apply_H(Xs, prec=fe.FE_F32)

@@ -98,6 +98,51 @@ def test_apply_H_f32_matches_oracle(fe, L, ncell, p, dirichlet, nvec, ld):
     assert_operator_entries(Y, ref, magnitude(H, X), 1e-6, "FP32 H X")
 
 
+# FP32-accurate tensor-core operator (FE_F32_F32ACC: in-plane contractions as split-TF32
+# tcgen05 MMAs, hi*hi + lo*hi + hi*lo, FP32 accumulation): the FP32 Frobenius bound and an
+# entry bound of 4e-6 (|Ht||X| units; the split products carry ~2^-22 per product, the
+# CUDA-core FP32 operator measures 2.5e-7)
+TC32_CASES = [c for c in F32_CASES if c[2] <= 5]
+
+
+@pytest.mark.parametrize("L,ncell,p,dirichlet", TC32_CASES)
+@pytest.mark.parametrize("nvec,ld", [(3, 4), (37, 40), (64, 64)])
+def test_apply_H_tc32_matches_oracle(fe, L, ncell, p, dirichlet, nvec, ld):
+    om, H, m, rng = _setup(fe, L, ncell, p, dirichlet, seed=1)
+    X = rng.standard_normal((om.n_psi, nvec)).astype(np.float32)
+    buf, Xg = _block(X, fe.FE_F32, fe, ld)
+    ybuf = torch.full_like(buf, 5.0)
+    fe._lib.call("fe_apply_H", m.handle, fe._ptr(buf), fe._ptr(ybuf), nvec, ld, fe.FE_F32_F32ACC)
+    ref = H @ X.astype(np.float64)
+    Y = ybuf[:, :nvec].double().cpu().numpy()
+    assert np.linalg.norm(Y - ref) / np.linalg.norm(ref) <= 2e-5
+    assert_operator_entries(Y, ref, magnitude(H, X), 4e-6, "split-TF32 H X")
+    if ld > nvec:
+        assert torch.all(ybuf[:, nvec:] == 5.0)
+
+
+def test_tc32_filter_and_refusals(fe):
+    """The tensor-core operator inside the fused filter (beta Z with Z = Y in place) against
+    the oracle, and its refusals: p = 6 (block beyond one MMA tile) and Bloch blocks."""
+    om, H, m, rng = _setup(fe, (5.0, 5.0, 10.0), (2, 2, 4), 5, (True, True), seed=8)
+    X = rng.standard_normal((om.n_psi, 16)).astype(np.float32).astype(np.float64)
+    lo, hi = chefsi.lanczos_bounds(lambda v: H @ v, rng.standard_normal(om.n_psi), 30)
+    a = lo + 0.1 * (hi - lo)
+    for degree in (1, 6):
+        ref = chefsi.cheb_filter(lambda Z: H @ Z, X, degree, a, hi, lo)
+        Xg = torch.tensor(X, dtype=torch.float32, device="cuda")
+        m.cheb_filter(Xg, degree, a, hi, lo, prec=fe.FE_F32_F32ACC)
+        got = Xg.double().cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-4
+        assert_column_maxabs(got, ref, 2e-5, f"split-TF32 filter degree {degree}")
+    m6 = fe.Mesh((6.0, 6.0, 6.0), (2, 2, 2), 6)
+    m6.set_potential(torch.zeros(m6.n_psi, dtype=torch.float64, device="cuda"))
+    X6 = torch.zeros((m6.n_psi, 8), dtype=torch.float32, device="cuda")
+    with pytest.raises(fe.FeError) as e:
+        m6.apply_H(X6, prec=fe.FE_F32_F32ACC)
+    assert e.value.status == fe._lib.FE_EUNSUPPORTED
+
+
 def test_apply_H_is_deterministic(fe):
     om, H, m, rng = _setup(fe, (4.0, 4.0, 9.0), (2, 2, 4), 3, (True, True))
     X = torch.tensor(rng.standard_normal((om.n_psi, 24)), device="cuda")
