@@ -423,6 +423,54 @@ def conformant_step(m, slab, X0, a, b, a0, phi_mixed, flops_step, dev, fe):
             "eig_count": k}
 
 
+def filter_variants(m, slab, X, phi, a, b, a0, dev, fe):
+    """The benchmark slab's degree-m filter with the operator variants of the method, each
+    timed (after one untimed filter) with CUDA events on the mesh stream: the Bloch k-point
+    Hamiltonian at k = (0.1, 0.05) / bohr on the same block read as nvec / 2 complex
+    vectors, and the potential integrated by Gauss quadrature.  Nominal flops as the
+    metric's (the collocated operator's cell-matrix count on nvec lanes)."""
+    import torch
+    st = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    nvec, degree = slab.nvec, slab.degree
+    flops = nominal_flops_per_hx(slab, nvec) * degree
+    out = {}
+
+    def timed(blk):
+        m.cheb_filter(blk, degree, a, b, a0, prec=fe.FE_F32)
+        e0, e1 = ev(), ev()
+        e0.record(st)
+        m.cheb_filter(blk, degree, a, b, a0, prec=fe.FE_F32)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    Xw = X.clone()
+    try:
+        m.set_kpoint(0.1, 0.05)
+        ms = timed(torch.view_as_complex(Xw.view(m.n_psi, nvec // 2, 2)))
+        out["kpoint_filter"] = {"ms": ms, "ms_per_hx": ms / degree,
+                                "tflops": flops / (ms * 1e-3) / 1e12,
+                                "workload": f"k = (0.1, 0.05) / bohr, {nvec // 2} complex vectors"}
+    finally:
+        m.set_kpoint(0.0, 0.0)
+    vb = torch.empty(m.n_psi, dtype=torch.float64, device=dev)
+    _, _, _ = m.poisson_solve(slab.bias, rtol=POISSON_RTOL, phi=phi, vbare=vb)
+    try:
+        m.set_potential_quad(m.interp_quad(m.vbare_phi(phi, slab.bias)))
+        Xw.copy_(X)
+        ms = timed(Xw)
+        out["quadrature_filter"] = {"ms": ms, "ms_per_hx": ms / degree,
+                                    "tflops": flops / (ms * 1e-3) / 1e12,
+                                    "workload": f"V_bare at the {slab.p + 1}^3 Gauss points of "
+                                                "every cell"}
+    finally:
+        m.set_potential(vb)
+    del Xw
+    torch.cuda.empty_cache()
+    return out
+
+
 def sweep_measure(steps, warmup):
     """Batched bias sweep: 24 independent slabs of 8 x 8 x H cells (p = 4, 128 vectors),
     half under a constant field and half under a constrained potential difference, stepped
@@ -661,30 +709,40 @@ def run_gpu(args):
     cin, cout = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     out_done = [None, None]
 
+    e2e_marks = []
+
     def step_e2e(i):
         j = i % 2
         arrived = ev()
         cin.wait_stream(st)
         if out_done[j] is not None:
             cin.wait_event(out_done[j])
+        e = [ev() for _ in range(7)]
         with torch.cuda.stream(cin):
+            e[0].record(cin)
             Xbuf[j].copy_(Xh, non_blocking=True)
             arrived.record(cin)
+        e[1].record(st)
         m.poisson_solve(slab.bias, rtol=POISSON_RTOL, phi=phi, vbare=vb)
         set_pot()
+        e[2].record(st)
         st.wait_event(arrived)
+        e[3].record(st)
         m.cheb_filter(views[j], degree, a, b, a0, prec=prec)
+        e[4].record(st)
         eig = m.rayleigh_ritz(views[j], prec=prec)
         fin = ev()
         fin.record(st)
         cout.wait_event(fin)
         with torch.cuda.stream(cout):
+            e[5].record(cout)
             outs[j].copy_(Xbuf[j], non_blocking=True)
             eig_h.copy_(eig, non_blocking=True)
             eig.record_stream(cout)
             done = ev()
             done.record(cout)
         out_done[j] = done
+        e2e_marks.append((e, arrived, fin, done))
 
     torch.cuda.synchronize(dev)
     e2e_start, e2e_end = ev(), ev()
@@ -700,6 +758,16 @@ def run_gpu(args):
     e2e_ms, _ = reduce_over_ranks(dist, dev, e2e_ms, 0)
     e2e_val = aggregate_value(world, flops_step, e2e_ms)
     e2e_result_ok = bool(torch.equal(outs[(e2e_steps - 1) % 2], Xbuf[(e2e_steps - 1) % 2].cpu()))
+    e2e_phases = {"h2d": 0.0, "poisson_and_veff": 0.0, "wait_for_input": 0.0, "cheb_filter": 0.0,
+                  "cholqr_rr": 0.0, "d2h": 0.0}
+    for e, arrived, fin, done in e2e_marks:
+        e2e_phases["h2d"] += e[0].elapsed_time(arrived)
+        e2e_phases["poisson_and_veff"] += e[1].elapsed_time(e[2])
+        e2e_phases["wait_for_input"] += e[2].elapsed_time(e[3])
+        e2e_phases["cheb_filter"] += e[3].elapsed_time(e[4])
+        e2e_phases["cholqr_rr"] += e[4].elapsed_time(fin)
+        e2e_phases["d2h"] += e[5].elapsed_time(done)
+    e2e_phases = {k: v / max(len(e2e_marks), 1) for k, v in e2e_phases.items()}
     del Xbuf[1], views
     torch.cuda.empty_cache()
 
@@ -748,7 +816,9 @@ def run_gpu(args):
             and args.workload == "p5"):
         conformant = conformant_step(m, slab, X0, a, b, a0, phi, flops_step, dev, fe)
     sweep = None
+    variants = {}
     if rank == 0 and world == 1 and not args.no_extras and args.workload == "p5":
+        variants = filter_variants(m, slab, X, phi, a, b, a0, dev, fe)
         sweep = sweep_measure(max(2, min(args.steps, 3)), 2)
 
     cpu = None
@@ -782,7 +852,8 @@ def run_gpu(args):
                     "h2d_bytes_per_step": int(X0.numel() * X.element_size()),
                     "d2h_bytes_per_step": int(X0.numel() * X.element_size() + blk.shape[1] * 8),
                     "result": "Ritz values and the filtered, rotated block read back every "
-                              "step", "result_matches_device": e2e_result_ok},
+                              "step", "result_matches_device": e2e_result_ok,
+                    "phases_ms": e2e_phases},
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
@@ -790,7 +861,9 @@ def run_gpu(args):
         if conformant is not None:
             line["conformant"] = conformant
         if sweep is not None:
-            line["variants"] = {"sweep": sweep}
+            variants["sweep"] = sweep
+        if variants:
+            line["variants"] = variants
         print(json.dumps(line))
     if dist:
         dist.barrier()
