@@ -46,6 +46,36 @@ void fe_count_launch(int64_t n = 1);
                      #call, (int)s_);                                                  \
   } while (0)
 
+// ---- programmatic dependent launch ---------------------------------------------------------
+// Short kernels that run back to back on one stream (the float CG iteration) are launched with
+// programmatic stream serialization: the next kernel may be scheduled while the current one
+// drains, and waits at its entry (griddepcontrol.wait) until its predecessor has completed and
+// its writes are visible, so the ordering is exactly that of plain launches.  Each such kernel
+// also lets its own dependent be scheduled as soon as all of its CTAs have started.  In a
+// kernel launched without the attribute both instructions are no-ops.
+#ifdef __CUDACC__
+__device__ __forceinline__ void fe_pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+#endif
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t fe_launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 #define FE_TRY(expr)                  \
   do {                                \
     fe_status t_ = (expr);            \

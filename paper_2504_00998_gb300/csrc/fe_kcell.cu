@@ -39,6 +39,7 @@ template <int P>
 __global__ void __launch_bounds__(CellStrip<P>::NTHR)
 k_cell_apply(const CellCoef cf, const float* __restrict__ x, float* __restrict__ ycell, int nx,
              int ny, int NX, int NY) {
+  fe_pdl_enter();
   using S = CellStrip<P>;
   constexpr int N1 = S::N1, CX = S::CX, UW = S::UW;
   __shared__ float U[N1 * N1 * UW];               // [lz][ly][xl]
@@ -141,6 +142,7 @@ template <int P>
 __global__ void __launch_bounds__(256)
 k_cell_gather(const float* __restrict__ ycell, float* __restrict__ y, int nx, int ny, int nz,
               int NX, int NY) {
+  fe_pdl_enter();
   constexpr int N1 = P + 1;
   const int gx = blockIdx.x * 32 + threadIdx.x;
   const int gy = blockIdx.y * 8 + threadIdx.y;
@@ -179,12 +181,14 @@ fe_status cell_apply_p(const CellCoef& cf, const fe_mesh* m, const float* x, flo
   using S = CellStrip<P>;
   const int nstrip = (m->nx + S::CX - 1) / S::CX;
   if (m->ny > 65535 || m->nz > 65535) return fe_fail(FE_EINVAL, "cell operator: mesh too large");
-  k_cell_apply<P><<<dim3(nstrip, m->ny, m->nz), S::NTHR, 0, m->stream>>>(cf, x, ycell, m->nx,
-                                                                         m->ny, m->NX, m->NY);
+  // programmatic dependent launches (each kernel waits for its predecessor at entry)
+  FE_CUDA(fe_launch_pdl(k_cell_apply<P>, dim3(nstrip, m->ny, m->nz), dim3(S::NTHR), 0, m->stream,
+                        cf, x, ycell, m->nx, m->ny, m->NX, m->NY));
   fe_count_launch();
   const int planes = m->NZ < 65535 ? m->NZ : 65535;
-  k_cell_gather<P><<<dim3((m->NX + 31) / 32, (m->NY + 7) / 8, planes), dim3(32, 8), 0, m->stream>>>(
-      ycell, y, m->nx, m->ny, m->nz, m->NX, m->NY);
+  const float* yc = ycell;
+  FE_CUDA(fe_launch_pdl(k_cell_gather<P>, dim3((m->NX + 31) / 32, (m->NY + 7) / 8, planes),
+                        dim3(32, 8), 0, m->stream, yc, y, m->nx, m->ny, m->nz, m->NX, m->NY));
   fe_count_launch();
   FE_CUDA(cudaGetLastError());
   return FE_OK;

@@ -515,6 +515,7 @@ __global__ void k_precond4(float* __restrict__ r, float* __restrict__ z,
 // p = z + beta p (skipped once converged)
 __global__ void k_update_p4(float* __restrict__ p, const float* __restrict__ z, const CgState* s,
                             int64_t n4) {
+  fe_pdl_enter();
   if (s->done && s->alpha == 0.0) return;
   const float b = (float)s->beta;
   float4* p4 = reinterpret_cast<float4*>(p);
@@ -580,6 +581,7 @@ __device__ __forceinline__ double sum_partials_cg(const double* part, int np) {
 // p.q partials; the last block sets pq and alpha = r.z / p.q
 __global__ void k_psum4_alpha(const float* __restrict__ p, const float* __restrict__ q, int64_t n4,
                               double* __restrict__ part, CgState* s) {
+  fe_pdl_enter();
   const float4* p4 = reinterpret_cast<const float4*>(p);
   const float4* q4 = reinterpret_cast<const float4*>(q);
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -615,6 +617,7 @@ __global__ void k_update_xr4s(float* __restrict__ x, float* __restrict__ r,
                               const float* __restrict__ p, const float* __restrict__ q,
                               const unsigned char* __restrict__ mask, const CgState* s,
                               int64_t plane4, int nseg, int seglen, double* __restrict__ seg) {
+  fe_pdl_enter();
   const float a = (float)s->alpha;
   const int pl = blockIdx.x / nseg, sg = blockIdx.x - pl * nseg;
   const int64_t lo = (int64_t)pl * plane4 + (int64_t)sg * seglen;
@@ -657,6 +660,7 @@ __global__ void k_coarse_apply4(const double* __restrict__ seg, int nseg,
                                 const double* __restrict__ cnt, const double* __restrict__ Ainv,
                                 CgState* st, int project, int nz, double inv_n,
                                 float* __restrict__ yf) {
+  fe_pdl_enter();
   extern __shared__ double cb[];   // b[nz]
   double loc = 0.0;
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
@@ -691,6 +695,7 @@ __global__ void k_precond4s_beta(float* __restrict__ r, float* __restrict__ z,
                                  int64_t plane4, int nseg, int seglen,
                                  double* __restrict__ part_rz, double* __restrict__ part_rr,
                                  const float* __restrict__ yf) {
+  fe_pdl_enter();
   const float mean = project ? (float)s->mean : 0.f;
   const int pl = blockIdx.x / nseg, sg = blockIdx.x - pl * nseg;
   const int64_t lo = (int64_t)pl * plane4 + (int64_t)sg * seglen;
@@ -1149,20 +1154,38 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
     FE_TRY(apply_K_v(m, b.p, b.q));
     if constexpr (std::is_same<V, float>::value) {
       if (fused) {
-        k_psum4_alpha<<<fe::RED_BLOCKS, fe::RED_THREADS, 0, st>>>(b.p, b.q, n4, b.pa, b.s);
+        // (programmatic dependent launches: each kernel waits for its predecessor at entry)
+        const float* cp = b.p;
+        const float* cq = b.q;
+        FE_CUDA(fe_launch_pdl(k_psum4_alpha, dim3(fe::RED_BLOCKS), dim3(fe::RED_THREADS), 0, st,
+                              cp, cq, n4, b.pa, b.s));
         fe_count_launch();
-        k_update_xr4s<<<nzp * b.nseg, 256, 0, st>>>(b.x, b.r, b.p, b.q, b.mask, b.s, plane / 4,
-                                                    b.nseg, seglen, b.seg);
+        const unsigned char* cmask = b.mask;
+        const CgState* cs = b.s;
+        const int64_t pl4 = plane / 4;
+        FE_CUDA(fe_launch_pdl(k_update_xr4s, dim3(nzp * b.nseg), dim3(256), 0, st, b.x, b.r, cp, cq,
+                              cmask, cs, pl4, b.nseg, seglen, b.seg));
         fe_count_launch();
-        k_coarse_apply4<<<(nzp + 7) / 8, 256, sizeof(double) * nzp, st>>>(
-            b.seg, b.nseg, b.ccnt, b.Ainv, b.s, project, nzp, 1.0 / (double)n, b.cyf);
+        const double* cseg = b.seg;
+        const double* ccnt = b.ccnt;
+        const double* cAinv = b.Ainv;
+        const double inv_n = 1.0 / (double)n;
+        FE_CUDA(fe_launch_pdl(k_coarse_apply4, dim3((nzp + 7) / 8), dim3(256),
+                              sizeof(double) * nzp, st, cseg, b.nseg, ccnt, cAinv, b.s, project,
+                              nzp, inv_n, b.cyf));
         fe_count_launch();
         const int64_t nsegs = (int64_t)nzp * b.nseg;
-        k_precond4s_beta<<<nzp * b.nseg, 256, 0, st>>>(b.r, b.z, b.dinv, b.mask, b.s, project,
-                                                       plane / 4, b.nseg, seglen, b.seg + nsegs,
-                                                       b.seg + 2 * nsegs, b.cyf);
+        const float* cdinv = b.dinv;
+        const float* cyf = b.cyf;
+        double* prz = b.seg + nsegs;
+        double* prr = b.seg + 2 * nsegs;
+        FE_CUDA(fe_launch_pdl(k_precond4s_beta, dim3(nzp * b.nseg), dim3(256), 0, st, b.r, b.z,
+                              cdinv, cmask, b.s, project, pl4, b.nseg, seglen, prz, prr, cyf));
         fe_count_launch();
-        k_update_p4<<<fe::grid_for(n4), 256, 0, st>>>(b.p, b.z, b.s, n4); fe_count_launch();
+        const float* cz = b.z;
+        FE_CUDA(fe_launch_pdl(k_update_p4, dim3(fe::grid_for(n4)), dim3(256), 0, st, b.p, cz, cs,
+                              n4));
+        fe_count_launch();
         return FE_OK;
       }
     }
