@@ -115,6 +115,13 @@ enum { FE_PRECOND_JACOBI = 0, FE_PRECOND_JACOBI_PLANES = 1 };
  *     double CG finishes from the current phi.  The stopping test (rtol on the double
  *     residual) and so the accuracy of phi are those of FE_POISSON_F64. */
 enum { FE_POISSON_F64 = 0, FE_POISSON_MIXED = 1 };
+/*   FE_OPT_RR_EIGEN: dense symmetric eigensolver of the n x n projected matrix in
+ *     fe_rayleigh_ritz (double precision either way).  FE_RR_EIGEN_SYEVD (default):
+ *     divide-and-conquer (cuSOLVER syevd).  FE_RR_EIGEN_SYEVJ: cyclic Jacobi (cuSOLVER
+ *     syevj) to a residual tolerance of 1e-14 relative, at most 100 sweeps; FE_ECUDA if it
+ *     does not converge. */
+enum { FE_OPT_RR_EIGEN = 3 };
+enum { FE_RR_EIGEN_SYEVD = 0, FE_RR_EIGEN_SYEVJ = 1 };
 fe_status fe_set_option(fe_mesh* mesh, int option, int64_t value);
 
 /* Node coordinates in phi order, xyz_dev[n_phi][3] (Section 2.3 node layout). */

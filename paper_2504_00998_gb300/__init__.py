@@ -85,6 +85,12 @@ class Mesh:
         call("fe_set_option", self._h, _lib.FE_OPT_RR_PRODUCTS,
              _lib.FE_RR_PRODUCTS_TC32 if tensor_core else _lib.FE_RR_PRODUCTS_F64)
 
+    def set_rr_eigensolver(self, jacobi):
+        """Dense eigensolver of the projected matrix in Rayleigh-Ritz: divide-and-conquer
+        (False, the default) or cyclic Jacobi (True); double precision either way."""
+        call("fe_set_option", self._h, _lib.FE_OPT_RR_EIGEN,
+             _lib.FE_RR_EIGEN_SYEVJ if jacobi else _lib.FE_RR_EIGEN_SYEVD)
+
     def set_poisson_precond(self, planes):
         """Poisson CG preconditioner: Jacobi (False) or Jacobi plus the z-plane coarse
         solve (True, the default)."""

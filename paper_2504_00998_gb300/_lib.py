@@ -13,10 +13,11 @@ FE_OK, FE_EINVAL, FE_ENOMEM, FE_ECUDA, FE_ENOCONV, FE_EBREAKDOWN, FE_ETIMEOUT, F
 FE_F64, FE_F32, FE_BF16_F32ACC, FE_F32_F32ACC = range(4)
 FE_FACE_NEUMANN, FE_FACE_DIRICHLET = 0, 1
 FE_BIAS_CEF, FE_BIAS_CPD = 0, 1
-FE_OPT_RR_PRODUCTS, FE_OPT_POISSON_PRECOND, FE_OPT_POISSON_ARITH = 0, 1, 2
+FE_OPT_RR_PRODUCTS, FE_OPT_POISSON_PRECOND, FE_OPT_POISSON_ARITH, FE_OPT_RR_EIGEN = 0, 1, 2, 3
 FE_POISSON_F64, FE_POISSON_MIXED = 0, 1
 FE_RR_PRODUCTS_F64, FE_RR_PRODUCTS_TC32 = 0, 1
 FE_PRECOND_JACOBI, FE_PRECOND_JACOBI_PLANES = 0, 1
+FE_RR_EIGEN_SYEVD, FE_RR_EIGEN_SYEVJ = 0, 1
 
 STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_ENOCONV",
                 5: "FE_EBREAKDOWN", 6: "FE_ETIMEOUT", 7: "FE_EUNSUPPORTED"}

@@ -244,6 +244,8 @@ struct fe_mesh {
 
   // Rayleigh-Ritz block products for float storage: 0 double GEMMs, 1 tensor-core BF16x9
   int rr_products = 0;
+  int rr_eigen = 0;                 // FE_RR_EIGEN_SYEVD / FE_RR_EIGEN_SYEVJ
+  syevjInfo_t syevj_params = nullptr;
   // Poisson CG preconditioner: 0 Jacobi, 1 Jacobi plus the exact z-plane coarse solve
   int poisson_precond = 1;
   // Poisson arithmetic: 0 double CG, 1 float corrections with double residuals

@@ -326,6 +326,7 @@ extern "C" fe_status fe_mesh_destroy(fe_mesh* m) {
   cudaFree(m->d_mass);
   delete[] m->h_atoms;
   if (m->cublas) cublasDestroy(m->cublas);
+  if (m->syevj_params) cusolverDnDestroySyevjInfo(m->syevj_params);
   if (m->cusolver) cusolverDnDestroy(m->cusolver);
   if (m->aux_stream) cudaStreamDestroy(m->aux_stream);
   if (m->ev_fork) cudaEventDestroy(m->ev_fork);
@@ -369,6 +370,11 @@ extern "C" fe_status fe_set_option(fe_mesh* m, int option, int64_t value) {
       if (value != FE_POISSON_F64 && value != FE_POISSON_MIXED)
         return fe_fail(FE_EINVAL, "fe_set_option: bad Poisson arithmetic");
       m->poisson_arith = (int)value;
+      return FE_OK;
+    case FE_OPT_RR_EIGEN:
+      if (value != FE_RR_EIGEN_SYEVD && value != FE_RR_EIGEN_SYEVJ)
+        return fe_fail(FE_EINVAL, "fe_set_option: bad Rayleigh-Ritz eigensolver");
+      m->rr_eigen = (int)value;
       return FE_OK;
     default:
       return fe_fail(FE_EINVAL, "fe_set_option: unknown option %d", option);

@@ -99,6 +99,20 @@ fe_status gram(fe_mesh* m, const double* A, int64_t lda, const double* B, int64_
   return FE_OK;
 }
 
+// eigenpairs of the symmetric n x n matrix in w.Q (upper triangle): eigenvectors overwrite
+// w.Q, ascending eigenvalues into w.eig, the solver's status into w.info (checked by the
+// caller); divide-and-conquer or cyclic Jacobi (FE_OPT_RR_EIGEN)
+fe_status sym_eig(fe_mesh* m, int n, RrWs& w) {
+  if (m->rr_eigen == FE_RR_EIGEN_SYEVJ) {
+    FE_CUSOLVER(cusolverDnDsyevj(m->cusolver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n,
+                                 w.Q, n, w.eig, w.work, w.lwork, w.info, m->syevj_params));
+  } else {
+    FE_CUSOLVER(cusolverDnDsyevd(m->cusolver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n,
+                                 w.Q, n, w.eig, w.work, w.lwork, w.info));
+  }
+  return FE_OK;
+}
+
 // one (optionally shifted) scaled Cholesky-QR pass on the double block; *broke = 1 if the
 // Cholesky factorisation failed
 fe_status cholqr_pass(fe_mesh* m, double* X, int64_t ld, int64_t nvec, RrWs& w, double shift,
@@ -200,8 +214,7 @@ fe_status rr_small(fe_mesh* m, int64_t nvec, RrWs& w, double* eig, bool* ill, do
   FE_CUBLAS(cublasDtrsm(m->cublas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
                         CUBLAS_DIAG_NON_UNIT, n, n, &one, w.S, n, w.Q, n));
   k_symmetrize<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.Q, n); fe_count_launch();
-  FE_CUSOLVER(cusolverDnDsyevd(m->cusolver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n,
-                               w.Q, n, w.eig, w.work, w.lwork, w.info));
+  FE_TRY(sym_eig(m, n, w));
   // C = D R^-1 Q
   FE_CUBLAS(cublasDtrsm(m->cublas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
                         CUBLAS_DIAG_NON_UNIT, n, n, &one, w.S, n, w.Q, n));
@@ -209,7 +222,7 @@ fe_status rr_small(fe_mesh* m, int64_t nvec, RrWs& w, double* eig, bool* ill, do
   FE_CUDA(cudaMemcpyAsync(eig, w.eig, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
   FE_CUDA(cudaMemcpyAsync(&hinfo, w.info, sizeof(int), cudaMemcpyDeviceToHost, st));
   FE_CUDA(cudaStreamSynchronize(st));
-  if (hinfo != 0) return fe_fail(FE_ECUDA, "syevd info %d", hinfo);
+  if (hinfo != 0) return fe_fail(FE_ECUDA, "dense eigensolver info %d", hinfo);
   return FE_OK;
 }
 
@@ -276,7 +289,7 @@ fe_status rr_gram_path_tc32(fe_mesh* m, float* X, int64_t ld, const float* HX, i
 }
 
 fe_status rr_setup_small(fe_mesh* m, int n, RrWs& w) {
-  int lw_potrf = 0, lw_syevd = 0;
+  int lw_potrf = 0, lw_syevd = 0, lw_syevj = 0;
   void* wsp;
   FE_TRY(fe_ws(m, WS_RR_SMALL, sizeof(double) * ((size_t)2 * n * n + 2 * n) + 64, &wsp));
   w.S = (double*)wsp;
@@ -286,7 +299,17 @@ fe_status rr_setup_small(fe_mesh* m, int n, RrWs& w) {
   FE_CUSOLVER(cusolverDnDpotrf_bufferSize(m->cusolver, CUBLAS_FILL_MODE_UPPER, n, w.S, n, &lw_potrf));
   FE_CUSOLVER(cusolverDnDsyevd_bufferSize(m->cusolver, CUSOLVER_EIG_MODE_VECTOR,
                                           CUBLAS_FILL_MODE_UPPER, n, w.Q, n, w.eig, &lw_syevd));
-  w.lwork = lw_potrf > lw_syevd ? lw_potrf : lw_syevd;
+  if (m->rr_eigen == FE_RR_EIGEN_SYEVJ) {
+    if (!m->syevj_params) {
+      FE_CUSOLVER(cusolverDnCreateSyevjInfo(&m->syevj_params));
+      FE_CUSOLVER(cusolverDnXsyevjSetTolerance(m->syevj_params, 1e-14));
+      FE_CUSOLVER(cusolverDnXsyevjSetMaxSweeps(m->syevj_params, 100));
+    }
+    FE_CUSOLVER(cusolverDnDsyevj_bufferSize(m->cusolver, CUSOLVER_EIG_MODE_VECTOR,
+                                            CUBLAS_FILL_MODE_UPPER, n, w.Q, n, w.eig, &lw_syevj,
+                                            m->syevj_params));
+  }
+  w.lwork = std::max(lw_potrf, std::max(lw_syevd, lw_syevj));
   void* wk;
   FE_TRY(fe_ws(m, WS_TC, sizeof(double) * ((size_t)w.lwork + 8), &wk));
   w.work = (double*)wk;
@@ -324,8 +347,7 @@ fe_status fe_rr_f64(fe_mesh* m, double* X, int64_t nvec, int64_t ld, double* eig
   FE_TRY(fe_hx_step(m, X, HX, nullptr, nvec, ld, 1.0, 0.0, 0.0, FE_F64));
   FE_TRY(gram(m, X, ld, HX, ld, nvec, w.Q));
   k_symmetrize<<<fe::grid_for((int64_t)n * n), 256, 0, st>>>(w.Q, n); fe_count_launch();
-  FE_CUSOLVER(cusolverDnDsyevd(m->cusolver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, n,
-                               w.Q, n, w.eig, w.work, w.lwork, w.info));
+  FE_TRY(sym_eig(m, n, w));
   // X <- X Q:  A_new = Q^T A, into HX then copy back
   const double one = 1.0, zero = 0.0;
   FE_CUBLAS(cublasDgemm(m->cublas, CUBLAS_OP_T, CUBLAS_OP_N, n, (int)m->n_psi, n, &one, w.Q, n,
@@ -335,7 +357,7 @@ fe_status fe_rr_f64(fe_mesh* m, double* X, int64_t nvec, int64_t ld, double* eig
   int hinfo = 0;
   FE_CUDA(cudaMemcpyAsync(&hinfo, w.info, sizeof(int), cudaMemcpyDeviceToHost, st));
   FE_CUDA(cudaStreamSynchronize(st));
-  if (hinfo != 0) return fe_fail(FE_ECUDA, "syevd info %d", hinfo);
+  if (hinfo != 0) return fe_fail(FE_ECUDA, "dense eigensolver info %d", hinfo);
   return FE_OK;
 }
 

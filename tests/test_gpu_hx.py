@@ -245,3 +245,22 @@ def test_rayleigh_ritz_tensor_core_products_decline_an_ill_conditioned_block(fe)
     assert np.max(np.abs(lam - lam_ref)) <= 1e-5 * max(1.0, np.max(np.abs(lam_ref)))
     Q = Xg.double().cpu().numpy()
     assert np.max(np.abs(Q.T @ Q - np.eye(8))) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_rayleigh_ritz_jacobi_eigensolver_matches_oracle(fe, prec):
+    """The cyclic-Jacobi option for the projected eigenproblem gives the oracle's Ritz values
+    and an orthonormal block that diagonalises H, to the same bounds as divide-and-conquer."""
+    p_ = fe.FE_F64 if prec == "f64" else fe.FE_F32
+    om, H, m, rng = _setup(fe, (4.0, 4.0, 9.0), (2, 2, 4), 3, (True, True), seed=24)
+    m.set_rr_eigensolver(True)
+    X = rng.standard_normal((om.n_psi, 40)).astype(np.float32).astype(np.float64)
+    lam_ref, _ = chefsi.rayleigh_ritz(lambda Z: H @ Z, X)
+    Xg = torch.tensor(X, dtype=fe.storage_dtype(p_), device="cuda")
+    lam = m.rayleigh_ritz(Xg, prec=p_).cpu().numpy()
+    assert np.all(np.diff(lam) >= 0)
+    assert np.max(np.abs(lam - lam_ref)) <= (1e-8 if prec == "f64" else 1e-4)
+    Q = Xg.double().cpu().numpy()
+    assert np.max(np.abs(Q.T @ Q - np.eye(40))) <= (1e-10 if prec == "f64" else 1e-5)
+    if prec == "f64":
+        assert np.max(np.abs(Q.T @ (H @ Q) - np.diag(lam))) <= 1e-9
