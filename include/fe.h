@@ -122,6 +122,23 @@ enum { FE_POISSON_F64 = 0, FE_POISSON_MIXED = 1 };
  *     does not converge. */
 enum { FE_OPT_RR_EIGEN = 3 };
 enum { FE_RR_EIGEN_SYEVD = 0, FE_RR_EIGEN_SYEVJ = 1 };
+/*   FE_OPT_POISSON_ITER: how the float CG of FE_POISSON_MIXED runs its iterations.
+ *     FE_POISSON_ITER_PERSISTENT (default): one cooperative kernel runs the iterations
+ *     between two reliable updates, its steps separated by grid-wide barriers (each wait
+ *     bounded: a barrier that gives up ends the solve with FE_ETIMEOUT); used with the
+ *     plane coarse space when the device supports cooperative launches and the phi planes
+ *     hold a multiple of four nodes, otherwise the launch-per-step iteration runs.
+ *     FE_POISSON_ITER_LAUNCHES: one kernel launch per step (seven per iteration), replayed
+ *     from CUDA graphs.  The arithmetic of an iteration is the same; the dot products are
+ *     summed in another fixed order, so iterates agree to rounding, not bitwise. */
+enum { FE_OPT_POISSON_ITER = 4 };
+enum { FE_POISSON_ITER_PERSISTENT = 0, FE_POISSON_ITER_LAUNCHES = 1 };
+/*   FE_OPT_TEST_CG_STALL: a test aid for the bounded waits of the persistent iteration.  A
+ *     value b >= 0 makes block b of its grid return before the first grid barrier, so no
+ *     barrier completes: the other blocks' waits run out (2 s), the launch ends and the
+ *     solve returns FE_ETIMEOUT with the mesh still usable.  -1 (the default) turns it
+ *     off. */
+enum { FE_OPT_TEST_CG_STALL = 5 };
 fe_status fe_set_option(fe_mesh* mesh, int option, int64_t value);
 
 /* Node coordinates in phi order, xyz_dev[n_phi][3] (Section 2.3 node layout). */

@@ -123,6 +123,12 @@ class Mesh:
         call("fe_set_option", self._h, _lib.FE_OPT_POISSON_ARITH,
              _lib.FE_POISSON_MIXED if mixed else _lib.FE_POISSON_F64)
 
+    def set_poisson_persistent(self, persistent):
+        """Float CG iterations in one cooperative kernel between reliable updates (True, the
+        default) or one launch per step from CUDA graphs (False)."""
+        call("fe_set_option", self._h, _lib.FE_OPT_POISSON_ITER,
+             _lib.FE_POISSON_ITER_PERSISTENT if persistent else _lib.FE_POISSON_ITER_LAUNCHES)
+
     def node_coords(self):
         out = self._f64((self.n_phi, 3))
         call("fe_node_coords", self._h, _ptr(out))

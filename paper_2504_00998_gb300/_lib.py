@@ -14,6 +14,8 @@ FE_F64, FE_F32, FE_BF16_F32ACC, FE_F32_F32ACC = range(4)
 FE_FACE_NEUMANN, FE_FACE_DIRICHLET = 0, 1
 FE_BIAS_CEF, FE_BIAS_CPD = 0, 1
 FE_OPT_RR_PRODUCTS, FE_OPT_POISSON_PRECOND, FE_OPT_POISSON_ARITH, FE_OPT_RR_EIGEN = 0, 1, 2, 3
+FE_OPT_POISSON_ITER, FE_OPT_TEST_CG_STALL = 4, 5
+FE_POISSON_ITER_PERSISTENT, FE_POISSON_ITER_LAUNCHES = 0, 1
 FE_POISSON_F64, FE_POISSON_MIXED = 0, 1
 FE_RR_PRODUCTS_F64, FE_RR_PRODUCTS_TC32 = 0, 1
 FE_PRECOND_JACOBI, FE_PRECOND_JACOBI_PLANES = 0, 1

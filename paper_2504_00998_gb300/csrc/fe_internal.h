@@ -13,7 +13,7 @@
 
 #define FE_MAXP 6
 #define FE_MAXN1 (FE_MAXP + 1)
-#define FE_NWS 17   // workspace slots of a mesh
+#define FE_NWS 18   // workspace slots of a mesh
 
 // ---- error state ------------------------------------------------------------------------
 fe_status fe_fail(fe_status st, const char* fmt, ...);
@@ -250,6 +250,8 @@ struct fe_mesh {
   int poisson_precond = 1;
   // Poisson arithmetic: 0 double CG, 1 float corrections with double residuals
   int poisson_arith = 1;
+  int poisson_iter = 0;             // FE_POISSON_ITER_PERSISTENT / FE_POISSON_ITER_LAUNCHES
+  int cg_stall = -1;                // FE_OPT_TEST_CG_STALL
   FeNonlocal nl;            // nonlocal term (natoms == 0: none)
   // potential by Gauss quadrature (fe_quadpot.cu): Bq[q][i] = l_i(gauss point q), wq the
   // Gauss weights (p + 1 points); W = w |J| V at every cell's Gauss points; M^-1/2 at psi nodes
@@ -280,7 +282,8 @@ struct fe_mesh {
 
 enum { WS_CHEB = 0, WS_RR_X = 1, WS_RR_HX = 2, WS_RR_SMALL = 3, WS_CG = 4, WS_RED = 5,
        WS_LANCZOS = 6, WS_TC = 7, WS_TC_IMG = 8, WS_YCELL = 9, WS_RR_TC32 = 10,
-       WS_PCOARSE = 11, WS_NL = 12, WS_KCELL = 13, WS_XC = 14, WS_KPT = 15, WS_KTC = 16 };
+       WS_PCOARSE = 11, WS_NL = 12, WS_KCELL = 13, WS_XC = 14, WS_KPT = 15, WS_KTC = 16,
+       WS_CGF = 17 };
 
 fe_status fe_ws(fe_mesh* m, int slot, size_t bytes, void** out);
 // Rayleigh-Ritz of a complex (Bloch) block: nvec, ld count complex entries (fe_kpoint.cu)

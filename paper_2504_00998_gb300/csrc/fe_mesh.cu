@@ -371,6 +371,16 @@ extern "C" fe_status fe_set_option(fe_mesh* m, int option, int64_t value) {
         return fe_fail(FE_EINVAL, "fe_set_option: bad Poisson arithmetic");
       m->poisson_arith = (int)value;
       return FE_OK;
+    case FE_OPT_POISSON_ITER:
+      if (value != FE_POISSON_ITER_PERSISTENT && value != FE_POISSON_ITER_LAUNCHES)
+        return fe_fail(FE_EINVAL, "fe_set_option: bad Poisson iteration mode");
+      m->poisson_iter = (int)value;
+      return FE_OK;
+    case FE_OPT_TEST_CG_STALL:
+      if (value < -1 || value > 0x7fffffff)
+        return fe_fail(FE_EINVAL, "fe_set_option: bad stalled block");
+      m->cg_stall = (int)value;
+      return FE_OK;
     case FE_OPT_RR_EIGEN:
       if (value != FE_RR_EIGEN_SYEVD && value != FE_RR_EIGEN_SYEVJ)
         return fe_fail(FE_EINVAL, "fe_set_option: bad Rayleigh-Ritz eigensolver");

@@ -22,17 +22,14 @@
 #include <vector>
 
 #include "fe_blas.cuh"
+#include "fe_cg.cuh"
 #include "fe_internal.h"
 
 namespace {
 
 constexpr double FOUR_PI = 12.566370614359172;
 
-struct CgState {
-  double rz, rz_new, pq, rr, alpha, beta, bnorm2, tol2, mean;
-  int done, iters, maxit;
-  unsigned int ticket[2];   // finished-block counters of the single-pass reductions (0 at rest)
-};
+using fe_cg::CgState;
 
 struct PGeom {
   int NX, NY, NZ, p;
@@ -1069,11 +1066,12 @@ fe_status apply_K_v(fe_mesh* m, const float* x, float* y) { return fe_kcell_appl
 // CG_RESTARTED (the same, and the search direction restarts from the new preconditioned
 // residual).
 enum { CG_CONTINUE = 0, CG_STOP = 1, CG_REPLACED = 2, CG_RESTARTED = 3 };
+constexpr int PERSIST_ITERS = 4096;
 
 template <typename V, typename Hook>
 fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double tol2_abs,
                  int maxit, bool use_graph, cudaGraphExec_t* exec, int64_t* graph_kernels,
-                 CgState* out, Hook&& hook) {
+                 CgState* out, const fe_cg::FusedStop* stop, Hook&& hook) {
   if constexpr (std::is_same<V, float>::value) {
     // the float operator's scratch exists before any graph capture
     void* w = nullptr;
@@ -1217,8 +1215,13 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
     if (!p4) { k_update_p<V><<<gb, 256, 0, st>>>(b.p, b.z, b.s, n); fe_count_launch(); }
     return FE_OK;
   };
+  // the same iteration in one cooperative kernel per interval between the hook's actions
+  bool persist = false;
+  if constexpr (std::is_same<V, float>::value)
+    persist = fused && use_graph && m->poisson_iter == FE_POISSON_ITER_PERSISTENT &&
+              fe_cg::fused_available(m);
   const int per_graph = 16;
-  if (use_graph && !*exec) {
+  if (use_graph && !persist && !*exec) {
     cudaGraph_t graph = nullptr;
     FE_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     fe_status cst = FE_OK;
@@ -1255,6 +1258,12 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
   while (true) {
     FE_CUDA(cudaMemcpyAsync(out, b.s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     FE_CUDA(cudaStreamSynchronize(st));
+    if (persist) {
+      if (out->fused_err)
+        return fe_fail(FE_ETIMEOUT, "Poisson CG: a grid barrier of the persistent iteration "
+                       "gave up after %d iterations", out->iters);
+      launched = out->iters;
+    }
     int action = out->done ? CG_STOP : CG_CONTINUE;
     FE_TRY(hook(*out, &action));
     if (action == CG_STOP || launched >= maxit) break;
@@ -1262,7 +1271,15 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
       replaced(action == CG_RESTARTED);
       FE_CUDA(cudaGetLastError());
     }
-    if (use_graph) {
+    if (persist) {
+      if constexpr (std::is_same<V, float>::value) {
+        const fe_cg::FusedCg fb{b.x, b.r, b.z, b.p, b.q, b.dinv, b.mask, b.Ainv, b.ccnt, b.s,
+                                project};
+        const fe_cg::FusedStop none{-1.0, HUGE_VAL, maxit};
+        // at most PERSIST_ITERS iterations per launch, so the host regains control
+        FE_TRY(fe_cg::fused_run(m, fb, PERSIST_ITERS, stop ? *stop : none));
+      }
+    } else if (use_graph) {
       cudaError_t e = cudaGraphLaunch(*exec, st);
       if (e != cudaSuccess) return fe_fail(FE_ECUDA, "CG graph launch: %s", cudaGetErrorString(e));
       fe_count_launch(*graph_kernels);
@@ -1404,6 +1421,9 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
                     segp, cyf, nseg};
     double rr_last = rr;
     int it_last = 0, stalls = 0, breakdowns = 0;
+    // the persistent iteration returns as soon as one of the tests below would act
+    fe_cg::FusedStop stop{1e-4 * rr_last, 1e2 * rr_last, it_last + 512};
+    auto restop = [&]() { stop = fe_cg::FusedStop{1e-4 * rr_last, 1e2 * rr_last, it_last + 512}; };
     auto reliable = [&](const CgState& cs, int* action) -> fe_status {
       used = cs.iters;
       // A kept search direction that no longer matches the replaced residual can make the
@@ -1415,6 +1435,7 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
         FE_CUDA(cudaMemsetAsync(df, 0, sizeof(float) * n, st));
         if (++breakdowns >= 2 || cs.iters >= bc->max_iter) { *action = CG_STOP; return FE_OK; }
         it_last = cs.iters;
+        restop();
         k_to_float<<<gb, 256, 0, st>>>(r, rf, n); fe_count_launch();
         *action = CG_RESTARTED;
         return FE_OK;
@@ -1432,19 +1453,20 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
       const bool tracks = rr <= 4.0 * cs.rr;
       rr_last = rr;
       it_last = cs.iters;
+      restop();
       k_to_float<<<gb, 256, 0, st>>>(r, rf, n); fe_count_launch();
       *action = tracks ? CG_REPLACED : CG_RESTARTED;
       return FE_OK;
     };
     FE_TRY(cg_run<float>(m, bf, project, 0.0, tol2, bc->max_iter, use_graph, &gexec_f.e, &gk_f,
-                         &hs, reliable));
+                         &hs, &stop, reliable));
   }
   if (rr > tol2 && used < bc->max_iter) {
     // double CG from the current phi (the whole solve when the mixed mode is off)
     CgBuf<double> bd{phi, r, z, p, q, dinv, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv,
                      nullptr, nullptr, 0};
     FE_TRY(cg_run<double>(m, bd, project, bc->rtol, tol2, bc->max_iter - used, use_graph,
-                          &gexec_d.e, &gk_d, &hs, no_hook));
+                          &gexec_d.e, &gk_d, &hs, nullptr, no_hook));
     used += hs.iters;
     rr = hs.rr;
   }

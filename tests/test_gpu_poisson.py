@@ -205,3 +205,72 @@ def test_mixed_refinement_matches_double_cg(fe, kind, layout):
         out[mixed] = phi.cpu().numpy()
     ref = out[False]
     assert np.max(np.abs(out[True] - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def _bias_for(kind, L):
+    Lz = L[2]
+    return {"cef": W.Bias("cef", field=0.01),
+            "cpd": W.Bias("cpd", dV=0.05, zA=2.0, zB=Lz - 2.0),
+            "lcpd": W.Bias("cpd", dV=0.05, zA=2.0, zB=Lz - 2.0,
+                           patch=((1.0, 1.0), (0.6 * L[0], 0.7 * L[1])))}[kind]
+
+
+@pytest.mark.parametrize("kind,p,ncell", [("cef", 4, (3, 3, 12)), ("cpd", 2, (4, 4, 10)),
+                                          ("lcpd", 5, (2, 2, 8)), ("cef", 6, (2, 2, 6)),
+                                          ("lcpd", 1, (4, 4, 16)), ("cef", 3, (4, 4, 10))])
+def test_persistent_cg_matches_launch_per_step(fe, kind, p, ncell):
+    """The float CG run as one cooperative kernel per reliable-update interval reaches the
+    oracle's solution like the launch-per-step iteration, in about as many iterations
+    (the dot products are summed in another order) and with far fewer launches.  p = 1..6,
+    the three bias setups, phi planes of 16 to 400 nodes."""
+    L = (6.0, 6.0, 24.0)
+    base = W.small_slab(ncell=ncell, p=p, L=L, natoms=4, seed=21)
+    bias = _bias_for(kind, L)
+    slab = W.Slab(base.name, base.L, base.ncell, base.p, base.R, base.Z, bias)
+    om, K, M, X = _oracle(slab)
+    rho, b = potentials.densities(X, M, slab.R, slab.Z, slab.L)
+    f = 4 * math.pi * M * (rho + b)
+    if kind == "cef":
+        ref = poisson.solve_cef_direct(K, f, M)
+    else:
+        vl = potentials.vloc_minus_vsm(X, slab.R, slab.Z, slab.L)
+        mask, vals, _, _ = potentials.cpd_constraints(X, vl, bias, slab.L)
+        ref = poisson.solve_cpd_direct(K, f, mask, vals)
+    lib = fe.load()
+    m = fe.Mesh.from_slab(slab)
+    out = {}
+    for persistent in (False, True):
+        m.set_poisson_persistent(persistent)
+        n0 = lib.fe_kernel_launches()
+        phi, _, info = m.poisson_solve(bias, rtol=1e-12)
+        launches = lib.fe_kernel_launches() - n0
+        assert info.status == 0 and info.rel_residual <= 1e-12
+        phi = phi.cpu().numpy()
+        assert np.max(np.abs(phi - ref)) <= 1e-9 * np.max(np.abs(ref))
+        out[persistent] = (phi, info.iters, launches)
+    it_l, it_p = out[False][1], out[True][1]
+    assert abs(it_p - it_l) <= 0.1 * it_l + 3, (it_l, it_p)
+    assert out[True][2] < out[False][2] / 3, (out[False][2], out[True][2])
+
+
+def test_persistent_cg_bounded_wait_reports_timeout(fe):
+    """One block of the cooperative CG kernel leaves before its first grid barrier (the test
+    aid FE_OPT_TEST_CG_STALL): no barrier can complete, the other blocks' waits run out
+    after 2 s, and the solve returns FE_ETIMEOUT instead of hanging; the mesh then solves
+    normally."""
+    import time
+    slab = W.small_slab(ncell=(2, 2, 8), p=4, L=(4.0, 4.0, 16.0), natoms=2, seed=3)
+    m = fe.Mesh.from_slab(slab)
+    fe.call("fe_set_option", m._h, fe._lib.FE_OPT_TEST_CG_STALL, 1)
+    t0 = time.time()
+    with pytest.raises(fe.FeError) as e:
+        m.poisson_solve(slab.bias, rtol=1e-12)
+    assert e.value.status == fe._lib.FE_ETIMEOUT
+    assert time.time() - t0 < 60
+    fe.call("fe_set_option", m._h, fe._lib.FE_OPT_TEST_CG_STALL, -1)
+    phi, _, info = m.poisson_solve(slab.bias, rtol=1e-12)
+    assert info.status == 0 and info.rel_residual <= 1e-12
+    m.set_poisson_persistent(False)
+    phi_l, _, _ = m.poisson_solve(slab.bias, rtol=1e-12)
+    ref = phi_l.cpu().numpy()
+    assert np.max(np.abs(phi.cpu().numpy() - ref)) <= 1e-9 * np.max(np.abs(ref))
