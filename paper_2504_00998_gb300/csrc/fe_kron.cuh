@@ -216,6 +216,8 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
   C* W1 = B + BYn * ARS * NCH;                                 // [BYn][WRS][NCH]
   C* W2 = W1 + BYn * WRS * NCH;
   C* Zr = W2 + BYn * WRS * NCH;                                // [ZR][BYn][BXn][NCH]
+  // the shape-table variants are launched for the mass-scaled Hamiltonian only
+  const bool mass_scale = CT || cf.mass_scale;
   const bool use_z = io.Z != nullptr;                          // (beta != 0 by launch)
   const bool use_v = io.V != nullptr;
   T* Vs = reinterpret_cast<T*>(Zr + (use_z ? TL::ZR * NZI : 0));   // [NSB][BYn][BXn]
@@ -253,6 +255,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
   int64_t it_node[IPT];     // in-plane node index of the output
   int64_t it_yo[IPT];       // offset of the item's entries in a plane of Y
   T it_sxy[IPT], it_isxy[IPT];
+  int it_w[IPT], it_v[IPT], it_s[IPT];   // the item's offsets in W1 / W2, a V plane, a stage
   C acc[IPT][P + 1];
 #pragma unroll
   for (int i = 0; i < IPT; ++i) {
@@ -267,8 +270,11 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
     it_own[i] = valid && (FULL || ((x0 + it_x[i] < g.NX) && (y0 + it_y[i] < g.NY) && (v0 < io.nvec)));
     it_node[i] = (x0 + it_x[i]) + (int64_t)g.NX * (y0 + it_y[i]);
     it_yo[i] = it_node[i] * io.ldy + v0;
-    it_sxy[i] = cf.mass_scale ? cf.sig[it_x[i] % P] * cf.sig[it_y[i] % P] : T(1);
+    it_sxy[i] = mass_scale ? cf.sig[it_x[i] % P] * cf.sig[it_y[i] % P] : T(1);
     it_isxy[i] = T(1) / it_sxy[i];
+    it_w[i] = (it_y[i] * TL::WRS + it_x[i]) * NCH + it_ch[i];
+    it_v[i] = it_y[i] * BXn + it_x[i];
+    it_s[i] = ((it_y[i] + P) * BXH + (it_x[i] + P)) * NCH + it_ch[i];
 #pragma unroll
     for (int j = 0; j <= P; ++j) acc[i][j].zero();
   }
@@ -293,45 +299,89 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
 
   // stage plane gz: the halo block of X into the stage buffer, V and the Chebyshev operand
   // of the owned nodes into their rings
+  // (called for gz = gbeg, gbeg + 1, ... in order: offsets and ring slots advance by one plane)
+  int64_t st_xoff = (int64_t)(gbeg - g.gz_lo) * plane_nodes * io.ldx;
+  const int64_t st_xstride = plane_nodes * io.ldx;
+  int st_slot = 0;                   // (gz - gbeg) % NSB of the plane to stage
+  int st_zslot = gbeg % TL::ZR;      // gz % ZR of the plane to stage
+  // the thread's V node and Z chunk offsets within a plane, and their plane offsets
+  int64_t st_voff = (int64_t)(gbeg - g.gz_lo) * plane_nodes;
+  int64_t st_zoff = st_voff * io.ldz;
+  const int64_t st_zstride = plane_nodes * io.ldz;
+  int64_t v_in = 0;
+  bool v_ok = false;
+  if (tid < BXn * BYn) {
+    const int x = tid % BXn, y = tid / BXn;
+    v_ok = FULL || (x0 + x < g.NX && y0 + y < g.NY);
+    v_in = (x0 + x) + (int64_t)g.NX * (y0 + y);
+  }
+  int64_t z_in[IPT];
+  int z_nb[IPT];
+#pragma unroll
+  for (int i = 0; i < IPT; ++i) {
+    const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
+    const int64_t rem = io.nvec - v0;
+    z_nb[i] = !it_own[i] ? 0 : (FULL ? CHB : (rem <= 0 ? 0 : (rem >= CH ? CHB : (int)(rem * sizeof(T)))));
+    z_in[i] = it_node[i] * io.ldz + v0;
+  }
   auto stage_plane = [&](int gz) {
+    const int64_t pbase = st_xoff, vbase = st_voff, zbase = st_zoff;
+    const int sslot = st_slot, zslot = st_zslot;
+    st_xoff += st_xstride;
+    st_voff += plane_nodes;
+    st_zoff += st_zstride;
+    st_slot = st_slot + 1 == TL::NSB ? 0 : st_slot + 1;
+    st_zslot = st_zslot + 1 == TL::ZR ? 0 : st_zslot + 1;
     if (!stored(gz)) return;
-    const int zs = gz - g.gz_lo;
-    const int64_t pbase = (int64_t)zs * plane_nodes * io.ldx;
-    C* dst = stage0 + ((gz - gbeg) % TL::NSB) * NST;
+    C* dst = stage0 + sslot * NST;
 #pragma unroll
     for (int i = 0; i < SPT; ++i) {
       const int e = tid + i * NTHR;
-      if (s_bytes[i] > 0) cp_async<CHB>(dst + e, io.X + pbase + s_goff[i], s_bytes[i]);
-      else if (s_bytes[i] == 0) cp_async<CHB>(dst + e, io.X, 0);
+      if constexpr (FULL && NST % NTHR == 0) {
+        // full tile, every thread stages SPT whole chunks
+        cp_async<CHB>(dst + e, io.X + pbase + s_goff[i], CHB);
+      } else {
+        if (s_bytes[i] > 0) cp_async<CHB>(dst + e, io.X + pbase + s_goff[i], s_bytes[i]);
+        else if (s_bytes[i] == 0) cp_async<CHB>(dst + e, io.X, 0);
+      }
     }
     if (use_v && tid < BXn * BYn) {
-      const int x = tid % BXn, y = tid / BXn;
-      T* vd = Vs + ((gz - gbeg) % TL::NSB) * (BXn * BYn) + tid;
-      const bool ok = FULL || (x0 + x < g.NX && y0 + y < g.NY);
-      const int64_t nid = (int64_t)zs * plane_nodes + (x0 + x) + (int64_t)g.NX * (y0 + y);
-      cp_async<(int)sizeof(T)>(vd, ok ? io.V + nid : io.V, ok ? (int)sizeof(T) : 0);
+      T* vd = Vs + sslot * (BXn * BYn) + tid;
+      if constexpr (FULL)
+        cp_async<(int)sizeof(T)>(vd, io.V + vbase + v_in, (int)sizeof(T));
+      else
+        cp_async<(int)sizeof(T)>(vd, v_ok ? io.V + vbase + v_in : io.V, v_ok ? (int)sizeof(T) : 0);
     }
     if (use_z && owned_plane(gz)) {
-      C* zd = Zr + (gz % TL::ZR) * NZI;
+      C* zd = Zr + zslot * NZI;
 #pragma unroll
       for (int i = 0; i < IPT; ++i) {
         const int item = tid + i * NTHR;
         if (item >= NZI) continue;
-        const int64_t v0 = vt0 + (int64_t)it_ch[i] * CH;
-        const int64_t rem = io.nvec - v0;
-        const int nb = !it_own[i] ? 0 : (FULL ? CHB : (rem <= 0 ? 0 : (rem >= CH ? CHB : (int)(rem * sizeof(T)))));
-        const T* src = nb ? io.Z + ((int64_t)zs * plane_nodes + it_node[i]) * io.ldz + v0 : io.Z;
-        cp_async<CHB>(zd + item, src, nb);
+        if constexpr (FULL) {
+          cp_async<CHB>(zd + item, io.Z + zbase + z_in[i], CHB);
+        } else {
+          const int nb = z_nb[i];
+          const T* src = nb ? io.Z + zbase + z_in[i] : io.Z;
+          cp_async<CHB>(zd + item, src, nb);
+        }
       }
     }
   };
 
   // write the final value of output plane gzo held in acc[i][j]
+  // layer c's bottom plane c P: its Z ring slot (c P) % ZR
+  int wr_zbase = (cb * P) % TL::ZR;
   auto write_plane = [&](int gzo, int j) {
     if (!owned_plane(gzo)) return;
     const int zs = gzo - g.gz_lo;
-    const T ps = cf.zout * rsq_of(gzo);
-    const C* zsrc = Zr + (gzo % TL::ZR) * NZI;
+    T rs = T(1);
+    if (mass_scale)
+      rs = j != 0 ? cf.rsq[j] : ((gzo == 0 || gzo == g.nz * P) ? cf.rsq_face : cf.rsq[0]);
+    const T ps = cf.zout * rs;
+    int zsl = wr_zbase + j;
+    zsl -= zsl >= TL::ZR ? TL::ZR : 0;
+    const C* zsrc = Zr + zsl * NZI;
     T* yplane = io.Y + (int64_t)zs * plane_nodes * io.ldy;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
@@ -377,8 +427,8 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
 #pragma unroll
       for (int i = 0; i < IPT; ++i) {
         if (pot && it_own[i]) {
-          const T pv = (vv[it_y[i] * BXn + it_x[i]] - io.shift) * inv_ps * it_isxy[i];
-          const C xs = st[((it_y[i] + P) * BXH + (it_x[i] + P)) * NCH + it_ch[i]];
+          const T pv = (vv[it_v[i]] - io.shift) * inv_ps * it_isxy[i];
+          const C xs = st[it_s[i]];
           acc[i][K].fma(pv, xs);
         }
         C a = w1[i], b = w2[i];
@@ -449,7 +499,8 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
   stage_plane(gbeg);
   cp_commit();
   int c = cb;
-  for (int gz = gbeg; gz <= gend; ++gz) {
+  int cur_slot = 0;   // (gz - gbeg) % NSB
+  for (int gz = gbeg; gz <= gend; ++gz, cur_slot = cur_slot + 1 == TL::NSB ? 0 : cur_slot + 1) {
     const int k = gz - c * P;
     if (gz < gend) {
       stage_plane(gz + 1);
@@ -459,7 +510,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
       cp_wait<0>();
     }
     __syncthreads();
-    const C* st = stage0 + ((gz - gbeg) % TL::NSB) * NST;
+    const C* st = stage0 + cur_slot * NST;
 
     if (stored(gz)) {
       // The two in-plane phases run on scalar lanes: an item is one cell segment of one
@@ -571,13 +622,18 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
       C w1[IPT], w2[IPT];
 #pragma unroll
       for (int i = 0; i < IPT; ++i) {
-        const int item = (it_y[i] * WRS + it_x[i]) * NCH + it_ch[i];
+        const int item = it_w[i];
         w1[i] = W1[item];
         w2[i] = W2[item];
       }
       const bool face = gz == 0 || gz == g.nz * P;
-      const T inv_ps = sq_of(gz) * cf.izout;
-      const T* vv = Vs + ((gz - gbeg) % TL::NSB) * (BXn * BYn);
+      T sqz = T(1);
+      if (mass_scale) {
+        const int l = k == P ? 0 : k;   // gz % P
+        sqz = l != 0 ? cf.sq[l] : (face ? cf.sq_face : cf.sq[0]);
+      }
+      const T inv_ps = sqz * cf.izout;
+      const T* vv = Vs + cur_slot * (BXn * BYn);
       dispatch_z(k, use_v, face, inv_ps, vv, st, w1, w2);
       if (k == P) {
         // the layer is complete: its first P planes are final; the top plane's sum
@@ -586,6 +642,8 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
         for (int j = 0; j < P; ++j) write_plane(c * P + j, j);
         shift_layer();
         ++c;
+        wr_zbase += P;
+        wr_zbase -= wr_zbase >= TL::ZR ? TL::ZR : 0;
         if (c < c1) dispatch_z(0, false, face, inv_ps, vv, st, w1, w2);
       }
     } else if (k == P) {
@@ -594,6 +652,8 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
       for (int j = 0; j < P; ++j) write_plane(c * P + j, j);
       shift_layer();
       ++c;
+      wr_zbase += P;
+      wr_zbase -= wr_zbase >= TL::ZR ? TL::ZR : 0;
     }
   }
   // the last processed plane (gend = c1 P) is final only if it is the top face
