@@ -98,14 +98,23 @@ fe_status fe_mesh_set_stream(fe_mesh* mesh, void* stream);
 enum { FE_OPT_RR_PRODUCTS = 0, FE_OPT_POISSON_PRECOND = 1, FE_OPT_POISSON_ARITH = 2 };
 enum { FE_RR_PRODUCTS_F64 = 0, FE_RR_PRODUCTS_TC32 = 1 };
 /*   FE_OPT_POISSON_PRECOND: preconditioner of the Poisson CG.  FE_PRECOND_JACOBI: the
- *     diagonal of K.  FE_PRECOND_JACOBI_PLANES (default): the diagonal plus an exact solve
+ *     diagonal of K.  FE_PRECOND_JACOBI_PLANES: the diagonal plus an exact solve
  *     on the coarse space of z-planes (one basis function per phi plane: the indicator of
  *     its free nodes), i.e. M^-1 = D^-1 + R^T (R K R^T)^-1 R with R the free-node plane
  *     sums.  The coarse matrix is banded (planes within one cell layer couple) and is
  *     factorised once per solve.  It removes the slow modes that are constant over x and y,
  *     which dominate on long slabs.  The converged solution is the same; only the
  *     iteration count changes. */
-enum { FE_PRECOND_JACOBI = 0, FE_PRECOND_JACOBI_PLANES = 1 };
+/*     FE_PRECOND_JACOBI_PLANES_MODES (default): the plane coarse space enriched, on every
+ *     plane, with the in-plane Fourier modes of wavenumber one (cos and sin of 2 pi x / Lx
+ *     and of 2 pi y / Ly on the plane's nodes); on a mesh without constrained phi nodes (the
+ *     CEF setup) they are decoupled from one another by the cell-translation invariance of
+ *     K, so each is one more exact nz x nz coarse solve.  Used by the persistent float
+ *     iteration (FE_OPT_POISSON_ITER) on such meshes when they span at least 8 cells along
+ *     both x and y (on narrower slabs these modes are not slow ones) and the planes hold a
+ *     multiple of four nodes along x; elsewhere it acts as FE_PRECOND_JACOBI_PLANES.  Built
+ *     once per mesh and constraint set (4 x (2p + 1) more double operator applications). */
+enum { FE_PRECOND_JACOBI = 0, FE_PRECOND_JACOBI_PLANES = 1, FE_PRECOND_JACOBI_PLANES_MODES = 2 };
 /*   FE_OPT_POISSON_ARITH: arithmetic of the Poisson solve.  FE_POISSON_F64: CG in double.
  *     FE_POISSON_MIXED (default): a float CG (operator, vectors and preconditioner in float,
  *     dot products accumulated in double) with reliable updates -- whenever its residual has

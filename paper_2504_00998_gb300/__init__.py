@@ -91,11 +91,14 @@ class Mesh:
         call("fe_set_option", self._h, _lib.FE_OPT_RR_EIGEN,
              _lib.FE_RR_EIGEN_SYEVJ if jacobi else _lib.FE_RR_EIGEN_SYEVD)
 
-    def set_poisson_precond(self, planes):
-        """Poisson CG preconditioner: Jacobi (False) or Jacobi plus the z-plane coarse
-        solve (True, the default)."""
-        call("fe_set_option", self._h, _lib.FE_OPT_POISSON_PRECOND,
-             _lib.FE_PRECOND_JACOBI_PLANES if planes else _lib.FE_PRECOND_JACOBI)
+    def set_poisson_precond(self, planes, modes=False):
+        """Poisson CG preconditioner: Jacobi (planes False), Jacobi plus the z-plane coarse
+        solve (planes True), and with modes True also the in-plane Fourier modes of
+        wavenumber one on every plane (persistent float iteration, meshes without
+        constrained phi nodes)."""
+        v = (_lib.FE_PRECOND_JACOBI_PLANES_MODES if modes else _lib.FE_PRECOND_JACOBI_PLANES) \
+            if planes else _lib.FE_PRECOND_JACOBI
+        call("fe_set_option", self._h, _lib.FE_OPT_POISSON_PRECOND, v)
 
     def planar(self, f, average=False):
         """Per phi plane: the planar integral (rho0) or average (V0) of a phi-node field."""

@@ -18,7 +18,7 @@ FE_OPT_POISSON_ITER, FE_OPT_TEST_CG_STALL = 4, 5
 FE_POISSON_ITER_PERSISTENT, FE_POISSON_ITER_LAUNCHES = 0, 1
 FE_POISSON_F64, FE_POISSON_MIXED = 0, 1
 FE_RR_PRODUCTS_F64, FE_RR_PRODUCTS_TC32 = 0, 1
-FE_PRECOND_JACOBI, FE_PRECOND_JACOBI_PLANES = 0, 1
+FE_PRECOND_JACOBI, FE_PRECOND_JACOBI_PLANES, FE_PRECOND_JACOBI_PLANES_MODES = 0, 1, 2
 FE_RR_EIGEN_SYEVD, FE_RR_EIGEN_SYEVJ = 0, 1
 
 STATUS_NAMES = {0: "FE_OK", 1: "FE_EINVAL", 2: "FE_ENOMEM", 3: "FE_ECUDA", 4: "FE_ENOCONV",

@@ -25,6 +25,11 @@ struct FusedCg {
   const double* cnt;    // free nodes per plane
   CgState* s;
   int project;          // CEF: residuals are kept at zero mean
+  // in-plane mode coarse space (nullptr: the plane indicators alone): the inverses of the
+  // four mode coarse matrices [4][nz][nz] (cos x, sin x, cos y, sin y) and the float mode
+  // tables (cos x, sin x [NX]; cos y, sin y [NY])
+  const double* Amodes;
+  const float* mtab;
 };
 
 // Early stop of a persistent launch: it returns after the first iteration whose float

@@ -61,11 +61,26 @@ struct FusedShape {
   // aligned
   static constexpr int GROUP_FLOATS =
       (CellStrip<P>::U_FLOATS + 2 * CellStrip<P>::A_FLOATS + 3) / 4 * 4;
-  // dynamic shared bytes for nzp phi planes
-  static constexpr size_t smem(int nzp) {
-    return sizeof(double) * (size_t)nzp + sizeof(float) * (size_t)NG * GROUP_FLOATS;
-  }
 };
+
+// dynamic shared memory of a block: the coarse right-hand sides [NM][nzp] (doubles), the mode
+// tables (NM > 1: cos x, sin x [NX], cos y, sin y [NY], floats), then from byte offset
+// group_offset() the strip groups' U, A, B
+// (the tables start on a 16-byte boundary: they are read four entries at a time)
+__host__ __device__ inline size_t table_offset(int NM, int nzp) {
+  return (sizeof(double) * (size_t)NM * nzp + 15) / 16 * 16;
+}
+template <int NM>
+inline size_t group_offset(int nzp, int NX, int NY) {
+  size_t b = table_offset(NM, nzp);
+  if (NM > 1) b += sizeof(float) * 2 * ((size_t)NX + NY);
+  return (b + 15) / 16 * 16;
+}
+template <int P, int NM>
+inline size_t fused_smem(int nzp, int NX, int NY) {
+  return group_offset<NM>(nzp, NX, NY) + sizeof(float) * (size_t)FusedShape<P>::NG *
+                                             FusedShape<P>::GROUP_FLOATS;
+}
 
 // grid-wide results published by the block that completes a barrier
 struct __align__(16) Pub {
@@ -95,6 +110,9 @@ struct FArgs {
   int nit, iters_stop;
   double rr_lo, rr_hi;
   int stall;                  // test aid: this block leaves before the first barrier (-1: none)
+  const double* Amodes;       // (NM > 1) mode coarse inverses [NM - 1][nzp][nzp]
+  const float* mtab;          // (NM > 1) mode tables: cos x, sin x [NX]; cos y, sin y [NY]
+  unsigned int grp_off;       // byte offset of the strip groups in dynamic shared memory
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* a) {
@@ -260,22 +278,29 @@ __device__ __forceinline__ float pick_slot(const float (&v)[N], int s) {
 // nodes (step 2) per thread and batch: independent loads in flight per thread
 constexpr int UB2 = 2;
 
-template <int P>
+// NM: coarse functions per plane (1: the plane indicator; 5: with the in-plane modes)
+template <int P, int NM>
 __global__ void __launch_bounds__(FusedShape<P>::NT, BLOCKS_PER_SM)
 k_cg_fused(const CellCoef cf, const FArgs a) {
   using S = CellStrip<P>;
   using F = FusedShape<P>;
   constexpr int NT = F::NT, GT = F::GT, NG = F::NG;
-  __shared__ double red[MAXSPAN];
-  __shared__ float redf[MAXSPAN * 64];
-  __shared__ float yv[MAXSPAN];
+  constexpr int NR = MAXSPAN > NM ? MAXSPAN : NM;   // values of one block reduction
+  __shared__ double red[NR];
+  __shared__ float redf[NR * 64];
+  __shared__ float yv[MAXSPAN * NM];
   // the block's copy of the published results; at entry, the state
   __shared__ Pub sp;
   __shared__ int maxit;
   __shared__ double tol2;
-  // dynamic: the coarse right-hand side [nzp] (doubles), then per strip group its U, A, B
+  // dynamic: the coarse right-hand sides [NM][nzp] (doubles), the mode tables, then per
+  // strip group its U, A, B
   extern __shared__ double dsm[];
   double* cb = dsm;
+  float* mcx = reinterpret_cast<float*>(reinterpret_cast<char*>(dsm) + table_offset(NM, a.nzp));
+  float* msx = mcx + a.NX;
+  float* mcy = msx + a.NX;
+  float* msy = mcy + a.NY;
   const int G = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
   const uint32_t plane = (uint32_t)a.NX * (uint32_t)a.NY;
   const uint32_t plane4 = plane / 4;
@@ -305,6 +330,9 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
     // of them; every block copies the whole after each)
     if (bid == 0) *a.pub = sp;
   }
+  if constexpr (NM > 1) {
+    for (int i = tid; i < 2 * (a.NX + a.NY); i += NT) mcx[i] = a.mtab[i];
+  }
   __syncthreads();
   if (sp.done || bid == a.stall) return;
 
@@ -322,7 +350,8 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
     // ---- 1. cell products of the search direction (a strip per thread group) ----------
     {
       const int g = tid / GT, gt = tid - g * GT;
-      float* Ug = reinterpret_cast<float*>(dsm + a.nzp) + (size_t)g * F::GROUP_FLOATS;
+      float* Ug = reinterpret_cast<float*>(reinterpret_cast<char*>(dsm) + a.grp_off) +
+                  (size_t)g * F::GROUP_FLOATS;
       float* Ag = Ug + S::U_FLOATS;
       float* Bg = Ag + S::A_FLOATS;
       auto sync = [g] { asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(GT) : "memory"); };
@@ -398,10 +427,7 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
     // ---- 3. x, r update; per-plane sums of r; the coarse right-hand side ------------------
     {
       const float af = sp.alphaf;
-      float ps[MAXSPAN];
-#pragma unroll
-      for (int j = 0; j < MAXSPAN; ++j) ps[j] = 0.f;
-      for (uint32_t k = c0 + tid; k < c1; k += NT) {
+      auto update = [&](uint32_t k) -> float4 {
         float4 xv = ldcg4(x4 + k), rv = ldcg4(r4 + k);
         const float4 pv = ldcg4(p4 + k), qv = ldcg4(q4 + k);
         const uchar4 mv = m4[k];
@@ -411,30 +437,70 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
         if (!mv.w) { xv.w += af * pv.w; rv.w -= af * qv.w; }
         x4[k] = xv;
         r4[k] = rv;
-        add_slot<MAXSPAN>(ps, (int)(k / plane4) - pl0, sum4(rv));
+        return rv;
+      };
+      if constexpr (NM == 1) {
+        float ps[MAXSPAN];
+#pragma unroll
+        for (int j = 0; j < MAXSPAN; ++j) ps[j] = 0.f;
+        for (uint32_t k = c0 + tid; k < c1; k += NT)
+          add_slot<MAXSPAN>(ps, (int)(k / plane4) - pl0, sum4(update(k)));
+        block_sum_f<MAXSPAN>(ps, red, redf);
+        if (tid < MAXSPAN) a.seg[(int64_t)bid * MAXSPAN + tid] = red[tid];
+      } else {
+        // plane by plane: the sums of r against the plane's NM coarse functions (the
+        // indicator, then cos x, sin x, cos y, sin y); a group of four nodes lies in one row
+        for (int sl = 0; sl < nsp; ++sl) {
+          const uint32_t pb = (uint32_t)(pl0 + sl) * plane4;
+          const uint32_t lo = max(c0, pb), hi = min(c1, pb + plane4);
+          float ms[NM];
+#pragma unroll
+          for (int j = 0; j < NM; ++j) ms[j] = 0.f;
+          for (uint32_t k = lo + tid; k < hi; k += NT) {
+            const float4 rv = update(k);
+            const uint32_t i4 = (k - pb) * 4;
+            const uint32_t gy = i4 / (uint32_t)a.NX, gx = i4 - gy * (uint32_t)a.NX;
+            const float4 cx = *reinterpret_cast<const float4*>(mcx + gx);
+            const float4 sx = *reinterpret_cast<const float4*>(msx + gx);
+            const float s0 = sum4(rv);
+            ms[0] += s0;
+            ms[1] += rv.x * cx.x + rv.y * cx.y + rv.z * cx.z + rv.w * cx.w;
+            ms[2] += rv.x * sx.x + rv.y * sx.y + rv.z * sx.z + rv.w * sx.w;
+            ms[3] += mcy[gy] * s0;
+            ms[4] += msy[gy] * s0;
+          }
+          block_sum_f<NM>(ms, red, redf);
+          if (tid < NM) a.seg[((int64_t)bid * MAXSPAN + sl) * NM + tid] = red[tid];
+        }
       }
-      block_sum_f<MAXSPAN>(ps, red, redf);
-      if (tid < MAXSPAN) a.seg[(int64_t)bid * MAXSPAN + tid] = red[tid];
     }
     {
-      // plane k's sum over the blocks whose nodes meet it (in block order), the mean under
-      // the CEF projection, b_k = sum - mean cnt_k
+      // the sums of each plane k over the blocks whose nodes meet it (in block order), the
+      // mean under the CEF projection, b_k = sum - mean cnt_k (the mode functions sum to
+      // zero over a plane, so only the indicator's right-hand side carries the mean)
       auto fin = [&] {
         for (int k = tid; k < a.nzp; k += NT) {
           const uint32_t g0 = (uint32_t)k * plane4, g1 = g0 + plane4 - 1;
           const int b0 = (int)(g0 / a.chunk4), b1 = (int)(g1 / a.chunk4);
-          double sk = 0.0;
-          for (int b = b0; b <= b1; ++b) {
-            const int slot = k - (int)(((uint32_t)b * a.chunk4) / plane4);
-            sk += __ldcg(a.seg + (int64_t)b * MAXSPAN + slot);
+#pragma unroll
+          for (int md = 0; md < NM; ++md) {
+            double sk = 0.0;
+            for (int b = b0; b <= b1; ++b) {
+              const int slot = k - (int)(((uint32_t)b * a.chunk4) / plane4);
+              sk += __ldcg(a.seg + ((int64_t)b * MAXSPAN + slot) * NM + md);
+            }
+            cb[md * a.nzp + k] = sk;
           }
-          cb[k] = sk;
         }
         __syncthreads();
         double t[1];
         sum_parts<1, true>(cb, 0, a.nzp, t, red);
         const double mn = a.project ? t[0] * a.inv_n : 0.0;
-        for (int k = tid; k < a.nzp; k += NT) a.cbg[k] = cb[k] - mn * a.cnt[k];
+        for (int k = tid; k < a.nzp; k += NT) {
+          a.cbg[k] = cb[k] - mn * a.cnt[k];
+#pragma unroll
+          for (int md = 1; md < NM; ++md) a.cbg[md * a.nzp + k] = cb[md * a.nzp + k];
+        }
         if (tid == 0) {
           a.pub->mean = mn;
           a.pub->meanf = (float)mn;
@@ -445,15 +511,19 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
 
     // ---- 4. coarse correction, preconditioner, r.z and r.r ------------------------------
     {
-      for (int k = tid; k < a.nzp; k += NT) cb[k] = __ldcg(a.cbg + k);
+      for (int k = tid; k < NM * a.nzp; k += NT) cb[k] = __ldcg(a.cbg + k);
       __syncthreads();
-      // the coarse values y_j = sum_k Ainv[j][k] b_k of the block's planes, warp j for
-      // plane pl0 + j (lane l takes k = l, l + 32, ... in order, then a shuffle tree)
+      // the coarse values of the block's planes, warp w for plane pl0 + w / NM and coarse
+      // function w % NM: y = sum_k Ainv[j][k] b_k (lane l takes k = l, l + 32, ... in order,
+      // then a shuffle tree)
       const int w = tid >> 5, lane = tid & 31;
-      if (w < nsp) {
-        const double* row = a.Ainv + (int64_t)(pl0 + w) * a.nzp;
+      if (w < nsp * NM) {
+        const int sl = w / NM, md = w - sl * NM;
+        const double* inv = md == 0 ? a.Ainv : a.Amodes + (size_t)(md - 1) * a.nzp * a.nzp;
+        const double* row = inv + (int64_t)(pl0 + sl) * a.nzp;
+        const double* bk = cb + md * a.nzp;
         double y = 0.0;
-        for (int k = lane; k < a.nzp; k += 32) y += row[k] * cb[k];
+        for (int k = lane; k < a.nzp; k += 32) y += row[k] * bk[k];
         y = warp_sum_d(y);
         if (lane == 0) yv[w] = (float)y;
       }
@@ -461,24 +531,36 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
     }
     {
       const float meanf = sp.meanf;
-      float cvs[MAXSPAN];
-#pragma unroll
-      for (int j = 0; j < MAXSPAN; ++j) cvs[j] = yv[j];
       float a1 = 0.f, a2 = 0.f;
       for (uint32_t k = c0 + tid; k < c1; k += NT) {
         float4 ri = ldcg4(r4 + k);
         const float4 dv = d4[k];
         const uchar4 mv = m4[k];
-        const float cv = pick_slot<MAXSPAN>(cvs, (int)(k / plane4) - pl0);
+        const int sl = (int)(k / plane4) - pl0;
+        float4 cv;
+        if constexpr (NM == 1) {
+          cv.x = cv.y = cv.z = cv.w = yv[sl];
+        } else {
+          const float* yy = yv + sl * NM;
+          const uint32_t i4 = (k - (uint32_t)(pl0 + sl) * plane4) * 4;
+          const uint32_t gy = i4 / (uint32_t)a.NX, gx = i4 - gy * (uint32_t)a.NX;
+          const float4 cx = *reinterpret_cast<const float4*>(mcx + gx);
+          const float4 sx = *reinterpret_cast<const float4*>(msx + gx);
+          const float base = yy[0] + yy[3] * mcy[gy] + yy[4] * msy[gy];
+          cv.x = base + yy[1] * cx.x + yy[2] * sx.x;
+          cv.y = base + yy[1] * cx.y + yy[2] * sx.y;
+          cv.z = base + yy[1] * cx.z + yy[2] * sx.z;
+          cv.w = base + yy[1] * cx.w + yy[2] * sx.w;
+        }
         if (a.project) {
           ri.x -= meanf; ri.y -= meanf; ri.z -= meanf; ri.w -= meanf;
           r4[k] = ri;
         }
         float4 zi;
-        zi.x = mv.x ? 0.f : dv.x * ri.x + cv;
-        zi.y = mv.y ? 0.f : dv.y * ri.y + cv;
-        zi.z = mv.z ? 0.f : dv.z * ri.z + cv;
-        zi.w = mv.w ? 0.f : dv.w * ri.w + cv;
+        zi.x = mv.x ? 0.f : dv.x * ri.x + cv.x;
+        zi.y = mv.y ? 0.f : dv.y * ri.y + cv.y;
+        zi.z = mv.z ? 0.f : dv.z * ri.z + cv.z;
+        zi.w = mv.w ? 0.f : dv.w * ri.w + cv.w;
         z4[k] = zi;
         a1 += ri.x * zi.x + ri.y * zi.y + ri.z * zi.z + ri.w * zi.w;
         a2 += ri.x * ri.x + ri.y * ri.y + ri.z * ri.z + ri.w * ri.w;
@@ -550,12 +632,12 @@ struct Plan {
 
 // the co-resident grid for the mesh (false, with nothing recorded as an error, when the
 // persistent iteration cannot run: no cooperative launch, too many planes for the coarse
-// right-hand side in shared memory, no resident block)
-template <int P>
+// right-hand sides in shared memory, no resident block)
+template <int P, int NM>
 bool plan_for(const fe_mesh* m, Plan* pl) {
   using F = FusedShape<P>;
   if (m->NZ > 8192) return false;
-  const size_t smem = F::smem(m->NZ);
+  const size_t smem = fused_smem<P, NM>(m->NZ, m->NX, m->NY);
   if (smem > 200 * 1024) return false;
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   bool ok = cudaGetDevice(&dev) == cudaSuccess &&
@@ -563,10 +645,10 @@ bool plan_for(const fe_mesh* m, Plan* pl) {
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
             coop != 0 && sms > 0;
   if (ok)
-    ok = cudaFuncSetAttribute(k_cg_fused<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    ok = cudaFuncSetAttribute(k_cg_fused<P, NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem) == cudaSuccess;
   if (ok)
-    ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_fused<P>, F::NT, smem) ==
+    ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_fused<P, NM>, F::NT, smem) ==
              cudaSuccess && per_sm >= 1;
   if (!ok) {
     cudaGetLastError();
@@ -579,12 +661,12 @@ bool plan_for(const fe_mesh* m, Plan* pl) {
 
 bool plan(const fe_mesh* m, Plan* pl) {
   switch (m->p) {
-    case 1: return plan_for<1>(m, pl);
-    case 2: return plan_for<2>(m, pl);
-    case 3: return plan_for<3>(m, pl);
-    case 4: return plan_for<4>(m, pl);
-    case 5: return plan_for<5>(m, pl);
-    case 6: return plan_for<6>(m, pl);
+    case 1: return plan_for<1, 1>(m, pl);
+    case 2: return plan_for<2, 1>(m, pl);
+    case 3: return plan_for<3, 1>(m, pl);
+    case 4: return plan_for<4, 1>(m, pl);
+    case 5: return plan_for<5, 1>(m, pl);
+    case 6: return plan_for<6, 1>(m, pl);
     default: return false;
   }
 }
@@ -602,10 +684,9 @@ bool chunk_for(const fe_mesh* m, int grid, uint32_t* chunk4) {
   return true;
 }
 
-template <int P>
-fe_status run_p(fe_mesh* m, const fe_cg::FusedCg& b, int nit, const fe_cg::FusedStop& stop) {
-  Plan pl;
-  if (!plan_for<P>(m, &pl)) return fe_fail(FE_EUNSUPPORTED, "persistent CG: no co-resident grid");
+template <int P, int NM>
+fe_status launch(fe_mesh* m, const Plan& pl, const fe_cg::FusedCg& b, int nit,
+                 const fe_cg::FusedStop& stop) {
   FArgs a;
   a.x = b.x; a.r = b.r; a.z = b.z; a.p = b.p;
   a.q = b.q;
@@ -625,11 +706,14 @@ fe_status run_p(fe_mesh* m, const fe_cg::FusedCg& b, int nit, const fe_cg::Fused
   a.rr_lo = stop.rr_lo;
   a.rr_hi = stop.rr_hi;
   a.stall = m->cg_stall;
-  // workspace: partials, per-plane sums, the coarse right-hand side, the published results
+  a.Amodes = NM > 1 ? b.Amodes : nullptr;
+  a.mtab = NM > 1 ? b.mtab : nullptr;
+  a.grp_off = (unsigned int)group_offset<NM>(m->NZ, m->NX, m->NY);
+  // workspace: partials, per-plane sums, the coarse right-hand sides, the published results
   // and the barrier words (each on its own 128-byte line); the cell grid is the two-pass
   // operator's scratch
-  const size_t nsegs = (size_t)pl.grid * MAXSPAN;
-  const size_t nd = 3 * (size_t)pl.grid + nsegs + (size_t)a.nzp;
+  const size_t nsegs = (size_t)pl.grid * MAXSPAN * NM;
+  const size_t nd = 3 * (size_t)pl.grid + nsegs + (size_t)NM * a.nzp;
   const size_t off_pub = (sizeof(double) * nd + 127) / 128 * 128;
   const size_t off_bar = off_pub + 256;
   const size_t bytes = off_bar + 256;
@@ -647,10 +731,20 @@ fe_status run_p(fe_mesh* m, const fe_cg::FusedCg& b, int nit, const fe_cg::Fused
   FE_CUDA(cudaMemsetAsync(a.bar, 0, 256, m->stream));
   const CellCoef cf = fe_kc::cell_coef(m);
   void* args[] = {(void*)&cf, (void*)&a};
-  FE_CUDA(cudaLaunchCooperativeKernel((const void*)k_cg_fused<P>, dim3(pl.grid),
+  FE_CUDA(cudaLaunchCooperativeKernel((const void*)k_cg_fused<P, NM>, dim3(pl.grid),
                                       dim3(FusedShape<P>::NT), args, pl.smem, m->stream));
   fe_count_launch();
   return FE_OK;
+}
+
+// the mode coarse space needs planes whose groups of four nodes lie in one row
+template <int P>
+fe_status run_p(fe_mesh* m, const fe_cg::FusedCg& b, int nit, const fe_cg::FusedStop& stop) {
+  Plan pl;
+  if (b.Amodes && b.mtab && m->NX % 4 == 0 && plan_for<P, 5>(m, &pl))
+    return launch<P, 5>(m, pl, b, nit, stop);
+  if (!plan_for<P, 1>(m, &pl)) return fe_fail(FE_EUNSUPPORTED, "persistent CG: no co-resident grid");
+  return launch<P, 1>(m, pl, b, nit, stop);
 }
 
 }  // namespace

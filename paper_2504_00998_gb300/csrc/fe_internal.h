@@ -13,7 +13,7 @@
 
 #define FE_MAXP 6
 #define FE_MAXN1 (FE_MAXP + 1)
-#define FE_NWS 18   // workspace slots of a mesh
+#define FE_NWS 19   // workspace slots of a mesh
 
 // ---- error state ------------------------------------------------------------------------
 fe_status fe_fail(fe_status st, const char* fmt, ...);
@@ -247,7 +247,7 @@ struct fe_mesh {
   int rr_eigen = 0;                 // FE_RR_EIGEN_SYEVD / FE_RR_EIGEN_SYEVJ
   syevjInfo_t syevj_params = nullptr;
   // Poisson CG preconditioner: 0 Jacobi, 1 Jacobi plus the exact z-plane coarse solve
-  int poisson_precond = 1;
+  int poisson_precond = 2;          // FE_PRECOND_JACOBI_PLANES_MODES
   // Poisson arithmetic: 0 double CG, 1 float corrections with double residuals
   int poisson_arith = 1;
   int poisson_iter = 0;             // FE_POISSON_ITER_PERSISTENT / FE_POISSON_ITER_LAUNCHES
@@ -264,6 +264,7 @@ struct fe_mesh {
 
   // cached coarse-space inverse (WS_PCOARSE): valid for the constraint set of pc_key
   int pc_state = 0;          // 0 none, 1 valid, 2 not SPD (Jacobi only for this key)
+  int pc_modes = 0;          // in-plane mode coarse space: 0 not built, 1 valid, 2 not used
   int pc_nz = 0;
   fe_poisson_bc pc_key = {};
 
@@ -283,7 +284,7 @@ struct fe_mesh {
 enum { WS_CHEB = 0, WS_RR_X = 1, WS_RR_HX = 2, WS_RR_SMALL = 3, WS_CG = 4, WS_RED = 5,
        WS_LANCZOS = 6, WS_TC = 7, WS_TC_IMG = 8, WS_YCELL = 9, WS_RR_TC32 = 10,
        WS_PCOARSE = 11, WS_NL = 12, WS_KCELL = 13, WS_XC = 14, WS_KPT = 15, WS_KTC = 16,
-       WS_CGF = 17 };
+       WS_CGF = 17, WS_PMODES = 18 };
 
 fe_status fe_ws(fe_mesh* m, int slot, size_t bytes, void** out);
 // Rayleigh-Ritz of a complex (Bloch) block: nvec, ld count complex entries (fe_kpoint.cu)

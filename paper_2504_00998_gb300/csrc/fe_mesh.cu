@@ -362,7 +362,8 @@ extern "C" fe_status fe_set_option(fe_mesh* m, int option, int64_t value) {
       m->rr_products = (int)value;
       return FE_OK;
     case FE_OPT_POISSON_PRECOND:
-      if (value != FE_PRECOND_JACOBI && value != FE_PRECOND_JACOBI_PLANES)
+      if (value != FE_PRECOND_JACOBI && value != FE_PRECOND_JACOBI_PLANES &&
+          value != FE_PRECOND_JACOBI_PLANES_MODES)
         return fe_fail(FE_EINVAL, "fe_set_option: bad Poisson preconditioner");
       m->poisson_precond = (int)value;
       return FE_OK;

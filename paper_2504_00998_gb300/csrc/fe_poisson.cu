@@ -776,6 +776,34 @@ __global__ void k_plane_color(const unsigned char* __restrict__ mask, int64_t pl
     v[i] = (!mask[i] && (int)((i / plane) % period) == color) ? 1.0 : 0.0;
 }
 
+// v = the coarse basis functions of in-plane mode (tx, ty) on the planes gz = color (mod
+// period): tx[gx] ty[gy] on their free nodes, 0 elsewhere
+__global__ void k_mode_color(const unsigned char* __restrict__ mask, int64_t plane, int NX,
+                             const double* __restrict__ tx, const double* __restrict__ ty,
+                             int period, int color, double* __restrict__ v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gz = i / plane, r = i - gz * plane;
+    const int gy = (int)(r / NX), gx = (int)(r - (int64_t)gy * NX);
+    v[i] = (!mask[i] && (int)(gz % period) == color) ? tx[gx] * ty[gy] : 0.0;
+  }
+}
+
+// out[j] = sum over the free nodes of plane j of tx[gx] ty[gy] x (one block per plane,
+// deterministic order)
+__global__ void k_mode_plane_sum(const double* __restrict__ x, const unsigned char* __restrict__ mask,
+                                 int64_t plane, int NX, const double* __restrict__ tx,
+                                 const double* __restrict__ ty, double* __restrict__ out) {
+  const int64_t base = (int64_t)blockIdx.x * plane;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < plane; i += fe::RED_THREADS) {
+    const int gy = (int)(i / NX), gx = (int)(i - (int64_t)gy * NX);
+    if (!mask[base + i]) a += tx[gx] * ty[gy] * x[base + i];
+  }
+  const double t = block_sum(a);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+
 constexpr int COARSE_COLS = 64;   // coarse unknowns per block of k_coarse_apply
 
 // y = Ainv (s - mean cnt): Ainv is the symmetric (pseudo-)inverse of the coarse matrix,
@@ -897,22 +925,124 @@ static bool same_constraints(const fe_poisson_bc& a, const fe_poisson_bc& b) {
 // planes (planes with free nodes; CEF: the last one is dropped to fix the constant), zero
 // elsewhere.  v and w are n-double scratch vectors.  *Ainv is nullptr when the coarse
 // space is off or its matrix is not numerically SPD.
+constexpr int MODES_MIN_CELLS = 8;
+
+// The in-plane modes of wavenumber one added to every plane's coarse function by
+// FE_PRECOND_JACOBI_PLANES_MODES: cos and sin of 2 pi x / Lx, then of 2 pi y / Ly.  On a
+// mesh without constrained phi nodes the cell-translation invariance of K decouples them
+// from one another and from the plane indicator, so each has its own nz x nz coarse matrix
+// R_m K R_m^T (built, like the plane matrix, from K applied to colourings of its basis
+// functions).  Workspace WS_PMODES: the four inverses, then the tables as float (cos x,
+// sin x [NX]; cos y, sin y [NY]) and as double (the same and the two ones tables).
+static fe_status modes_setup(fe_mesh* m, const unsigned char* mask, double* v, double* w,
+                             const double* hcnt, const double** Amodes, const float** mtab) {
+  const int nz = m->NZ, NX = m->NX, NY = m->NY;
+  const int64_t plane = (int64_t)NX * NY, n = m->n_phi;
+  for (int j = 0; j < nz; ++j)
+    if (hcnt[j] < (double)plane - 0.5) return FE_OK;   // constrained nodes: planes only
+  if (NX % 4 != 0) return FE_OK;
+  const size_t nzz = (size_t)nz * nz;
+  const size_t bytes = sizeof(double) * 4 * nzz + sizeof(float) * 2 * ((size_t)NX + NY) + 64 +
+                       sizeof(double) * 3 * ((size_t)NX + NY);
+  void* wsp;
+  FE_TRY(fe_ws(m, WS_PMODES, bytes, &wsp));
+  double* dAm = (double*)wsp;
+  float* dtab = (float*)(dAm + 4 * nzz);
+  double* dtd = (double*)(((uintptr_t)(dtab + 2 * (NX + NY)) + 63) & ~(uintptr_t)63);
+  // node coordinates along x and y (GLL points of each cell)
+  const double two_pi = 2.0 * 3.14159265358979323846;
+  std::vector<double> htd(3 * ((size_t)NX + NY));
+  std::vector<float> htab(2 * ((size_t)NX + NY));
+  const double Lx = m->nx * m->h[0], Ly = m->ny * m->h[1];
+  for (int g = 0; g < NX; ++g) {
+    const double x = (g / m->p) * m->h[0] + 0.5 * (m->xi[g % m->p] + 1.0) * m->h[0];
+    htd[g] = std::cos(two_pi * x / Lx);
+    htd[NX + g] = std::sin(two_pi * x / Lx);
+    htd[2 * NX + 2 * NY + g] = 1.0;
+  }
+  for (int g = 0; g < NY; ++g) {
+    const double y = (g / m->p) * m->h[1] + 0.5 * (m->xi[g % m->p] + 1.0) * m->h[1];
+    htd[2 * NX + g] = std::cos(two_pi * y / Ly);
+    htd[2 * NX + NY + g] = std::sin(two_pi * y / Ly);
+    htd[3 * NX + 2 * NY + g] = 1.0;
+  }
+  for (size_t i = 0; i < htab.size(); ++i) htab[i] = (float)htd[i];
+  cudaStream_t st = m->stream;
+  FE_CUDA(cudaMemcpyAsync(dtd, htd.data(), sizeof(double) * htd.size(), cudaMemcpyHostToDevice, st));
+  FE_CUDA(cudaMemcpyAsync(dtab, htab.data(), sizeof(float) * htab.size(), cudaMemcpyHostToDevice, st));
+  const double* ones_x = dtd + 2 * NX + 2 * NY;
+  const double* ones_y = ones_x + NX;
+  const double* tx[4] = {dtd, dtd + NX, ones_x, ones_x};
+  const double* ty[4] = {ones_y, ones_y, dtd + 2 * NX, dtd + 2 * NX + NY};
+  const int period = 2 * m->p + 1;
+  std::vector<double> wsum((size_t)period * nz);
+  void* sws;
+  FE_TRY(fe_ws(m, WS_PCOARSE, sizeof(double) * (nzz + 2 * (size_t)nz) + 64, &sws));
+  double* dsum = (double*)sws + nzz + nz;
+  for (int md = 0; md < 4; ++md) {
+    for (int c = 0; c < period; ++c) {
+      k_mode_color<<<fe::grid_for(n), 256, 0, st>>>(mask, plane, NX, tx[md], ty[md], period, c,
+                                                    v, n);
+      fe_count_launch();
+      FE_TRY(fe_poisson_apply_K(m, v, w));
+      k_mode_plane_sum<<<nz, fe::RED_THREADS, 0, st>>>(w, mask, plane, NX, tx[md], ty[md], dsum);
+      fe_count_launch();
+      FE_CUDA(cudaMemcpyAsync(wsum.data() + (size_t)c * nz, dsum, sizeof(double) * nz,
+                              cudaMemcpyDeviceToHost, st));
+    }
+    FE_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> A(nzz, 0.0);
+    for (int j = 0; j < nz; ++j)
+      for (int i = j - m->p; i <= j + m->p; ++i)
+        if (i >= 0 && i < nz) A[(size_t)j * nz + i] = wsum[(size_t)(i % period) * nz + j];
+    for (int a = 0; a < nz; ++a)
+      for (int b = 0; b < a; ++b) {
+        const double s2 = 0.5 * (A[(size_t)a * nz + b] + A[(size_t)b * nz + a]);
+        A[(size_t)a * nz + b] = A[(size_t)b * nz + a] = s2;
+      }
+    if (!spd_inverse(A, nz)) return FE_OK;   // (not expected: planes only)
+    FE_CUDA(cudaMemcpyAsync(dAm + md * nzz, A.data(), sizeof(double) * nzz,
+                            cudaMemcpyHostToDevice, st));
+    FE_CUDA(cudaStreamSynchronize(st));
+  }
+  *Amodes = dAm;
+  *mtab = dtab;
+  return FE_OK;
+}
+
 static fe_status coarse_setup(fe_mesh* m, const fe_poisson_bc* bc, const unsigned char* mask,
-                              double* v, double* w, const double** Ainv, const double** cnt) {
+                              double* v, double* w, const double** Ainv, const double** cnt,
+                              const double** Amodes, const float** mtab) {
   *Ainv = nullptr;
   *cnt = nullptr;
+  *Amodes = nullptr;
+  *mtab = nullptr;
   const int nz = m->NZ;
-  if (m->poisson_precond != FE_PRECOND_JACOBI_PLANES || nz > 2048) return FE_OK;
+  if ((m->poisson_precond != FE_PRECOND_JACOBI_PLANES &&
+       m->poisson_precond != FE_PRECOND_JACOBI_PLANES_MODES) || nz > 2048)
+    return FE_OK;
+  // (the wavenumber-one modes are slow modes of the Jacobi-preconditioned operator only when
+  // the slab spans many cells in x and y; on narrow slabs they would only add to the top of
+  // the preconditioned spectrum)
+  const bool want_modes = m->poisson_precond == FE_PRECOND_JACOBI_PLANES_MODES &&
+                          m->nx >= MODES_MIN_CELLS && m->ny >= MODES_MIN_CELLS;
   const int64_t plane = (int64_t)m->NX * m->NY, n = m->n_phi;
   void* wsp;
   FE_TRY(fe_ws(m, WS_PCOARSE, sizeof(double) * ((size_t)nz * nz + 2 * (size_t)nz) + 64, &wsp));
   double* dA = (double*)wsp;
   double* dcnt = dA + (size_t)nz * nz;
   double* dsum = dcnt + nz;
-  if (m->pc_state != 0 && m->pc_nz == nz && same_constraints(m->pc_key, *bc)) {
+  if (m->pc_state != 0 && m->pc_nz == nz && same_constraints(m->pc_key, *bc) &&
+      (!want_modes || m->pc_modes != 0)) {
     if (m->pc_state == 1) { *Ainv = dA; *cnt = dcnt; }
+    if (m->pc_state == 1 && want_modes && m->pc_modes == 1) {
+      char* mw = static_cast<char*>(m->ws[WS_PMODES]);
+      *Amodes = reinterpret_cast<const double*>(mw);
+      *mtab = reinterpret_cast<const float*>(mw + sizeof(double) * 4 * (size_t)nz * nz);
+    }
     return FE_OK;
   }
+  m->pc_modes = 0;
   cudaStream_t st = m->stream;
   const int period = 2 * m->p + 1;
   std::vector<double> wsum((size_t)period * nz), hcnt(nz);
@@ -950,6 +1080,7 @@ static fe_status coarse_setup(fe_mesh* m, const fe_poisson_bc* bc, const unsigne
   m->pc_nz = nz;
   if (na == 0 || !spd_inverse(A, na)) {
     m->pc_state = 2;
+    m->pc_modes = 2;
     return FE_OK;
   }
   std::vector<double> full((size_t)nz * nz, 0.0);
@@ -960,6 +1091,10 @@ static fe_status coarse_setup(fe_mesh* m, const fe_poisson_bc* bc, const unsigne
   m->pc_state = 1;
   *Ainv = dA;
   *cnt = dcnt;
+  if (want_modes) {
+    FE_TRY(modes_setup(m, mask, v, w, hcnt.data(), Amodes, mtab));
+    m->pc_modes = *Amodes ? 1 : 2;
+  }
   return FE_OK;
 }
 
@@ -1051,6 +1186,10 @@ struct CgBuf {
                                // the preconditioner's r.z and r.r partials (3 nz nseg doubles)
   float* cyf;                  // float coarse correction per plane
   int nseg;                    // segments per plane
+  // in-plane mode coarse space (persistent float iteration only; nullptr: planes only):
+  // the four mode inverses [4][nz][nz] and the float mode tables (cos x, sin x, cos y, sin y)
+  const double* Amodes;
+  const float* mtab;
 };
 
 fe_status apply_K_v(fe_mesh* m, const double* x, double* y) { return fe_poisson_apply_K(m, x, y); }
@@ -1274,7 +1413,7 @@ fe_status cg_run(fe_mesh* m, const CgBuf<V>& b, int project, double rtol, double
     if (persist) {
       if constexpr (std::is_same<V, float>::value) {
         const fe_cg::FusedCg fb{b.x, b.r, b.z, b.p, b.q, b.dinv, b.mask, b.Ainv, b.ccnt, b.s,
-                                project};
+                                project, b.Amodes, b.mtab};
         const fe_cg::FusedStop none{-1.0, HUGE_VAL, maxit};
         // at most PERSIST_ITERS iterations per launch, so the host regains control
         FE_TRY(fe_cg::fused_run(m, fb, PERSIST_ITERS, stop ? *stop : none));
@@ -1362,7 +1501,9 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   // coarse space of z-planes (z and q serve as scratch before the iteration starts)
   const double* Ainv = nullptr;
   const double* ccnt = nullptr;
-  FE_TRY(coarse_setup(m, bc, mask, z, q, &Ainv, &ccnt));
+  const double* Amodes = nullptr;
+  const float* mtab = nullptr;
+  FE_TRY(coarse_setup(m, bc, mask, z, q, &Ainv, &ccnt, &Amodes, &mtab));
   double* csum = Ainv ? (double*)(ccnt + nzp) : nullptr;
 
   // double residual r = f - K phi (masked; CEF: minus its mean) and |r|^2 on the host
@@ -1418,7 +1559,7 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
     k_to_float<<<gb, 256, 0, st>>>(r, rf, n); fe_count_launch();
     FE_CUDA(cudaMemsetAsync(df, 0, sizeof(float) * n, st));
     CgBuf<float> bf{df, rf, zf, pf, qf, dinvf, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv,
-                    segp, cyf, nseg};
+                    segp, cyf, nseg, Amodes, mtab};
     double rr_last = rr;
     int it_last = 0, stalls = 0, breakdowns = 0;
     // the persistent iteration returns as soon as one of the tests below would act
@@ -1464,7 +1605,7 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   if (rr > tol2 && used < bc->max_iter) {
     // double CG from the current phi (the whole solve when the mixed mode is off)
     CgBuf<double> bd{phi, r, z, p, q, dinv, mask, pa, pb, pc, pd, s, Ainv, ccnt, csum, cyv,
-                     nullptr, nullptr, 0};
+                     nullptr, nullptr, 0, nullptr, nullptr};
     FE_TRY(cg_run<double>(m, bd, project, bc->rtol, tol2, bc->max_iter - used, use_graph,
                           &gexec_d.e, &gk_d, &hs, nullptr, no_hook));
     used += hs.iters;
