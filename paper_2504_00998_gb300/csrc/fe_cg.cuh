@@ -8,6 +8,10 @@
 
 namespace fe_cg {
 
+// coarse functions per plane with the in-plane modes: the indicator, cos x, sin x, cos y,
+// sin y, cos x cos y, cos x sin y, sin x cos y, sin x sin y
+constexpr int MODES_NM = 9;
+
 struct CgState {
   double rz, rz_new, pq, rr, alpha, beta, bnorm2, tol2, mean;
   int done, iters, maxit;
@@ -26,9 +30,9 @@ struct FusedCg {
   CgState* s;
   int project;          // CEF: residuals are kept at zero mean
   // in-plane mode coarse space (nullptr: the plane indicators alone): the inverses of the
-  // four mode coarse matrices [4][nz][nz] (cos x, sin x, cos y, sin y) and the float mode
-  // tables (cos x, sin x [NX]; cos y, sin y [NY])
-  const double* Amodes;
+  // MODES_NM - 1 mode coarse matrices [MODES_NM - 1][nz][nz] (in the order above, float) and the
+  // float mode tables (cos x, sin x [NX]; cos y, sin y [NY])
+  const float* Amodes;
   const float* mtab;
 };
 

@@ -50,6 +50,9 @@ constexpr int BLOCKS_PER_SM = 2;
 // planes that the nodes of one block may span (the host falls back to the launch-per-step
 // iteration beyond this)
 constexpr int MAXSPAN = 4;
+// coarse functions per plane with the in-plane modes (the indicator and fe_cg::MODES_NM - 1
+// modes)
+constexpr int MODES_NM = fe_cg::MODES_NM;
 
 // threads of a block: NG strip groups of GT threads
 template <int P>
@@ -63,12 +66,13 @@ struct FusedShape {
       (CellStrip<P>::U_FLOATS + 2 * CellStrip<P>::A_FLOATS + 3) / 4 * 4;
 };
 
-// dynamic shared memory of a block: the coarse right-hand sides [NM][nzp] (doubles), the mode
-// tables (NM > 1: cos x, sin x [NX], cos y, sin y [NY], floats), then from byte offset
-// group_offset() the strip groups' U, A, B
+// dynamic shared memory of a block: the coarse right-hand side of the plane indicators [nzp]
+// (doubles) and (NM > 1) of the modes [NM - 1][nzp] (floats), the mode tables (cos x, sin x
+// [NX], cos y, sin y [NY], floats), then from byte offset group_offset() the strip groups'
+// U, A, B
 // (the tables start on a 16-byte boundary: they are read four entries at a time)
 __host__ __device__ inline size_t table_offset(int NM, int nzp) {
-  return (sizeof(double) * (size_t)NM * nzp + 15) / 16 * 16;
+  return (sizeof(double) * (size_t)nzp + sizeof(float) * (size_t)(NM - 1) * nzp + 15) / 16 * 16;
 }
 template <int NM>
 inline size_t group_offset(int nzp, int NX, int NY) {
@@ -110,7 +114,8 @@ struct FArgs {
   int nit, iters_stop;
   double rr_lo, rr_hi;
   int stall;                  // test aid: this block leaves before the first barrier (-1: none)
-  const double* Amodes;       // (NM > 1) mode coarse inverses [NM - 1][nzp][nzp]
+  const float* Amodes;        // (NM > 1) mode coarse inverses [NM - 1][nzp][nzp], float
+  float* cbgf;                // (NM > 1) the modes' coarse right-hand sides [NM - 1][nzp]
   const float* mtab;          // (NM > 1) mode tables: cos x, sin x [NX]; cos y, sin y [NY]
   unsigned int grp_off;       // byte offset of the strip groups in dynamic shared memory
 };
@@ -234,6 +239,33 @@ __device__ __forceinline__ void block_sum_f(const float (&v)[N], double* out, fl
   }
   __syncthreads();
 }
+// block sums of float terms in float (every thread reads out[0..N) after the trailing
+// barrier): a shuffle tree in each warp, then warp 0 adds the warp totals the same way; for
+// sums that only have to be a fixed linear function of their terms.  sh holds N * 32 floats.
+template <int N>
+__device__ __forceinline__ void block_sum_plain(const float (&v)[N], float* out, float* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    float d = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    if (lane == 0) sh[j * 32 + w] = d;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      float t = lane < nw ? sh[j * 32 + lane] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) out[j] = t;
+    }
+  }
+  __syncthreads();
+}
+
 // sums of the n doubles part[j * stride + i] (i < n) for j < N, by warp 0 (lane l takes
 // i = l, l + 32, ... in order, then a shuffle tree); every thread receives them.  part is
 // global memory (read through L2: other blocks wrote it) unless SHARED.  sh holds N doubles.
@@ -278,7 +310,9 @@ __device__ __forceinline__ float pick_slot(const float (&v)[N], int s) {
 // nodes (step 2) per thread and batch: independent loads in flight per thread
 constexpr int UB2 = 2;
 
-// NM: coarse functions per plane (1: the plane indicator; 5: with the in-plane modes)
+// NM: coarse functions per plane (1: the plane indicator; 5: with the in-plane modes cos x,
+// sin x, cos y, sin y; 9: also their products cos x cos y, cos x sin y, sin x cos y,
+// sin x sin y)
 template <int P, int NM>
 __global__ void __launch_bounds__(FusedShape<P>::NT, BLOCKS_PER_SM)
 k_cg_fused(const CellCoef cf, const FArgs a) {
@@ -463,14 +497,30 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
             const float4 cx = *reinterpret_cast<const float4*>(mcx + gx);
             const float4 sx = *reinterpret_cast<const float4*>(msx + gx);
             const float s0 = sum4(rv);
+            const float rc = rv.x * cx.x + rv.y * cx.y + rv.z * cx.z + rv.w * cx.w;
+            const float rs = rv.x * sx.x + rv.y * sx.y + rv.z * sx.z + rv.w * sx.w;
+            const float cy = mcy[gy], sy = msy[gy];
             ms[0] += s0;
-            ms[1] += rv.x * cx.x + rv.y * cx.y + rv.z * cx.z + rv.w * cx.w;
-            ms[2] += rv.x * sx.x + rv.y * sx.y + rv.z * sx.z + rv.w * sx.w;
-            ms[3] += mcy[gy] * s0;
-            ms[4] += msy[gy] * s0;
+            ms[1] += rc;
+            ms[2] += rs;
+            ms[3] += cy * s0;
+            ms[4] += sy * s0;
+            if constexpr (NM == 9) {
+              ms[5] += cy * rc;
+              ms[6] += sy * rc;
+              ms[7] += cy * rs;
+              ms[8] += sy * rs;
+            }
           }
-          block_sum_f<NM>(ms, red, redf);
-          if (tid < NM) a.seg[((int64_t)bid * MAXSPAN + sl) * NM + tid] = red[tid];
+          // the indicator's sum in float pairs (it also carries the mean), the modes' in float
+          const float m0[1] = {ms[0]};
+          block_sum_f<1>(m0, red, redf);
+          float mm[NM - 1];
+#pragma unroll
+          for (int j = 1; j < NM; ++j) mm[j - 1] = ms[j];
+          block_sum_plain<NM - 1>(mm, yv, redf);
+          if (tid < NM)
+            a.seg[((int64_t)bid * MAXSPAN + sl) * NM + tid] = tid == 0 ? red[0] : (double)yv[tid - 1];
         }
       }
     }
@@ -479,28 +529,24 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
       // mean under the CEF projection, b_k = sum - mean cnt_k (the mode functions sum to
       // zero over a plane, so only the indicator's right-hand side carries the mean)
       auto fin = [&] {
-        for (int k = tid; k < a.nzp; k += NT) {
+        // one (coarse function, plane) pair per thread and step
+        for (int e = tid; e < NM * a.nzp; e += NT) {
+          const int md = e / a.nzp, k = e - md * a.nzp;
           const uint32_t g0 = (uint32_t)k * plane4, g1 = g0 + plane4 - 1;
           const int b0 = (int)(g0 / a.chunk4), b1 = (int)(g1 / a.chunk4);
-#pragma unroll
-          for (int md = 0; md < NM; ++md) {
-            double sk = 0.0;
-            for (int b = b0; b <= b1; ++b) {
-              const int slot = k - (int)(((uint32_t)b * a.chunk4) / plane4);
-              sk += __ldcg(a.seg + ((int64_t)b * MAXSPAN + slot) * NM + md);
-            }
-            cb[md * a.nzp + k] = sk;
+          double sk = 0.0;
+          for (int b = b0; b <= b1; ++b) {
+            const int slot = k - (int)(((uint32_t)b * a.chunk4) / plane4);
+            sk += __ldcg(a.seg + ((int64_t)b * MAXSPAN + slot) * NM + md);
           }
+          if (md == 0) cb[k] = sk;
+          else a.cbgf[(md - 1) * a.nzp + k] = (float)sk;
         }
         __syncthreads();
         double t[1];
         sum_parts<1, true>(cb, 0, a.nzp, t, red);
         const double mn = a.project ? t[0] * a.inv_n : 0.0;
-        for (int k = tid; k < a.nzp; k += NT) {
-          a.cbg[k] = cb[k] - mn * a.cnt[k];
-#pragma unroll
-          for (int md = 1; md < NM; ++md) a.cbg[md * a.nzp + k] = cb[md * a.nzp + k];
-        }
+        for (int k = tid; k < a.nzp; k += NT) a.cbg[k] = cb[k] - mn * a.cnt[k];
         if (tid == 0) {
           a.pub->mean = mn;
           a.pub->meanf = (float)mn;
@@ -511,21 +557,32 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
 
     // ---- 4. coarse correction, preconditioner, r.z and r.r ------------------------------
     {
-      for (int k = tid; k < NM * a.nzp; k += NT) cb[k] = __ldcg(a.cbg + k);
+      for (int k = tid; k < a.nzp; k += NT) cb[k] = __ldcg(a.cbg + k);
+      float* cbf = reinterpret_cast<float*>(cb + a.nzp);   // (NM > 1) the modes' [NM - 1][nzp]
+      for (int k = tid; k < (NM - 1) * a.nzp; k += NT) cbf[k] = __ldcg(a.cbgf + k);
       __syncthreads();
       // the coarse values of the block's planes, warp w for plane pl0 + w / NM and coarse
       // function w % NM: y = sum_k Ainv[j][k] b_k (lane l takes k = l, l + 32, ... in order,
       // then a shuffle tree)
-      const int w = tid >> 5, lane = tid & 31;
-      if (w < nsp * NM) {
+      const int lane = tid & 31;
+      for (int w = tid >> 5; w < nsp * NM; w += NT / 32) {
         const int sl = w / NM, md = w - sl * NM;
-        const double* inv = md == 0 ? a.Ainv : a.Amodes + (size_t)(md - 1) * a.nzp * a.nzp;
-        const double* row = inv + (int64_t)(pl0 + sl) * a.nzp;
-        const double* bk = cb + md * a.nzp;
-        double y = 0.0;
-        for (int k = lane; k < a.nzp; k += 32) y += row[k] * bk[k];
-        y = warp_sum_d(y);
-        if (lane == 0) yv[w] = (float)y;
+        if (md == 0) {
+          const double* row = a.Ainv + (int64_t)(pl0 + sl) * a.nzp;
+          double y = 0.0;
+          for (int k = lane; k < a.nzp; k += 32) y += row[k] * cb[k];
+          y = warp_sum_d(y);
+          if (lane == 0) yv[w] = (float)y;
+        } else {
+          // the mode inverses in float (single precision suffices for the coarse correction)
+          const float* row = a.Amodes + ((size_t)(md - 1) * a.nzp + (pl0 + sl)) * a.nzp;
+          const float* bk = cbf + (md - 1) * a.nzp;
+          float y = 0.f;
+          for (int k = lane; k < a.nzp; k += 32) y = __fmaf_rn(row[k], bk[k], y);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+          if (lane == 0) yv[w] = y;
+        }
       }
       __syncthreads();
     }
@@ -546,11 +603,18 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
           const uint32_t gy = i4 / (uint32_t)a.NX, gx = i4 - gy * (uint32_t)a.NX;
           const float4 cx = *reinterpret_cast<const float4*>(mcx + gx);
           const float4 sx = *reinterpret_cast<const float4*>(msx + gx);
-          const float base = yy[0] + yy[3] * mcy[gy] + yy[4] * msy[gy];
-          cv.x = base + yy[1] * cx.x + yy[2] * sx.x;
-          cv.y = base + yy[1] * cx.y + yy[2] * sx.y;
-          cv.z = base + yy[1] * cx.z + yy[2] * sx.z;
-          cv.w = base + yy[1] * cx.w + yy[2] * sx.w;
+          const float cy = mcy[gy], sy = msy[gy];
+          // y0 + y1 cx + y2 sx + y3 cy + y4 sy (+ y5 cx cy + y6 cx sy + y7 sx cy + y8 sx sy)
+          const float base = yy[0] + yy[3] * cy + yy[4] * sy;
+          float fc = yy[1], fs = yy[2];
+          if constexpr (NM == 9) {
+            fc += yy[5] * cy + yy[6] * sy;
+            fs += yy[7] * cy + yy[8] * sy;
+          }
+          cv.x = base + fc * cx.x + fs * sx.x;
+          cv.y = base + fc * cx.y + fs * sx.y;
+          cv.z = base + fc * cx.z + fs * sx.z;
+          cv.w = base + fc * cx.w + fs * sx.w;
         }
         if (a.project) {
           ri.x -= meanf; ri.y -= meanf; ri.z -= meanf; ri.w -= meanf;
@@ -713,8 +777,9 @@ fe_status launch(fe_mesh* m, const Plan& pl, const fe_cg::FusedCg& b, int nit,
   // and the barrier words (each on its own 128-byte line); the cell grid is the two-pass
   // operator's scratch
   const size_t nsegs = (size_t)pl.grid * MAXSPAN * NM;
-  const size_t nd = 3 * (size_t)pl.grid + nsegs + (size_t)NM * a.nzp;
-  const size_t off_pub = (sizeof(double) * nd + 127) / 128 * 128;
+  const size_t nd = 3 * (size_t)pl.grid + nsegs + (size_t)a.nzp;
+  const size_t off_cbgf = (sizeof(double) * nd + 127) / 128 * 128;
+  const size_t off_pub = (off_cbgf + sizeof(float) * (size_t)(NM - 1) * a.nzp + 127) / 128 * 128;
   const size_t off_bar = off_pub + 256;
   const size_t bytes = off_bar + 256;
   void* w = nullptr;
@@ -723,6 +788,7 @@ fe_status launch(fe_mesh* m, const Plan& pl, const fe_cg::FusedCg& b, int nit,
   a.part = reinterpret_cast<double*>(wb);
   a.seg = a.part + 3 * (size_t)pl.grid;
   a.cbg = a.seg + nsegs;
+  a.cbgf = reinterpret_cast<float*>(wb + off_cbgf);
   a.pub = reinterpret_cast<Pub*>(wb + off_pub);
   a.bar = reinterpret_cast<unsigned int*>(wb + off_bar);
   void* yc = nullptr;
@@ -741,8 +807,8 @@ fe_status launch(fe_mesh* m, const Plan& pl, const fe_cg::FusedCg& b, int nit,
 template <int P>
 fe_status run_p(fe_mesh* m, const fe_cg::FusedCg& b, int nit, const fe_cg::FusedStop& stop) {
   Plan pl;
-  if (b.Amodes && b.mtab && m->NX % 4 == 0 && plan_for<P, 5>(m, &pl))
-    return launch<P, 5>(m, pl, b, nit, stop);
+  if (b.Amodes && b.mtab && m->NX % 4 == 0 && plan_for<P, MODES_NM>(m, &pl))
+    return launch<P, MODES_NM>(m, pl, b, nit, stop);
   if (!plan_for<P, 1>(m, &pl)) return fe_fail(FE_EUNSUPPORTED, "persistent CG: no co-resident grid");
   return launch<P, 1>(m, pl, b, nit, stop);
 }

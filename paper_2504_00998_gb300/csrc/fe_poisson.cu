@@ -928,26 +928,29 @@ static bool same_constraints(const fe_poisson_bc& a, const fe_poisson_bc& b) {
 constexpr int MODES_MIN_CELLS = 8;
 
 // The in-plane modes of wavenumber one added to every plane's coarse function by
-// FE_PRECOND_JACOBI_PLANES_MODES: cos and sin of 2 pi x / Lx, then of 2 pi y / Ly.  On a
-// mesh without constrained phi nodes the cell-translation invariance of K decouples them
-// from one another and from the plane indicator, so each has its own nz x nz coarse matrix
-// R_m K R_m^T (built, like the plane matrix, from K applied to colourings of its basis
-// functions).  Workspace WS_PMODES: the four inverses, then the tables as float (cos x,
-// sin x [NX]; cos y, sin y [NY]) and as double (the same and the two ones tables).
+// FE_PRECOND_JACOBI_PLANES_MODES: cos and sin of 2 pi x / Lx, of 2 pi y / Ly, and the four
+// products (cos x cos y, cos x sin y, sin x cos y, sin x sin y).  On a mesh without
+// constrained phi nodes the cell-translation invariance of K (and its reflection symmetry in
+// x and in y) decouples them from one another and from the plane indicator, so each has its
+// own nz x nz coarse matrix R_m K R_m^T (built, like the plane matrix, from K applied to
+// colourings of its basis functions).  Workspace WS_PMODES: the NM - 1 inverses (float),
+// then the tables as float (cos x, sin x [NX]; cos y, sin y [NY]) and as double (the same and
+// the two ones tables).
 static fe_status modes_setup(fe_mesh* m, const unsigned char* mask, double* v, double* w,
-                             const double* hcnt, const double** Amodes, const float** mtab) {
+                             const double* hcnt, const float** Amodes, const float** mtab) {
   const int nz = m->NZ, NX = m->NX, NY = m->NY;
   const int64_t plane = (int64_t)NX * NY, n = m->n_phi;
   for (int j = 0; j < nz; ++j)
     if (hcnt[j] < (double)plane - 0.5) return FE_OK;   // constrained nodes: planes only
   if (NX % 4 != 0) return FE_OK;
+  constexpr int NMOD = fe_cg::MODES_NM - 1;
   const size_t nzz = (size_t)nz * nz;
-  const size_t bytes = sizeof(double) * 4 * nzz + sizeof(float) * 2 * ((size_t)NX + NY) + 64 +
+  const size_t bytes = sizeof(float) * NMOD * nzz + sizeof(float) * 2 * ((size_t)NX + NY) + 64 +
                        sizeof(double) * 3 * ((size_t)NX + NY);
   void* wsp;
   FE_TRY(fe_ws(m, WS_PMODES, bytes, &wsp));
-  double* dAm = (double*)wsp;
-  float* dtab = (float*)(dAm + 4 * nzz);
+  float* dAm = (float*)wsp;   // the mode inverses in float (enough for a coarse correction)
+  float* dtab = dAm + NMOD * nzz;
   double* dtd = (double*)(((uintptr_t)(dtab + 2 * (NX + NY)) + 63) & ~(uintptr_t)63);
   // node coordinates along x and y (GLL points of each cell)
   const double two_pi = 2.0 * 3.14159265358979323846;
@@ -972,14 +975,19 @@ static fe_status modes_setup(fe_mesh* m, const unsigned char* mask, double* v, d
   FE_CUDA(cudaMemcpyAsync(dtab, htab.data(), sizeof(float) * htab.size(), cudaMemcpyHostToDevice, st));
   const double* ones_x = dtd + 2 * NX + 2 * NY;
   const double* ones_y = ones_x + NX;
-  const double* tx[4] = {dtd, dtd + NX, ones_x, ones_x};
-  const double* ty[4] = {ones_y, ones_y, dtd + 2 * NX, dtd + 2 * NX + NY};
+  const double* cxd = dtd;
+  const double* sxd = dtd + NX;
+  const double* cyd = dtd + 2 * NX;
+  const double* syd = dtd + 2 * NX + NY;
+  const double* tx[8] = {cxd, sxd, ones_x, ones_x, cxd, cxd, sxd, sxd};
+  const double* ty[8] = {ones_y, ones_y, cyd, syd, cyd, syd, cyd, syd};
+  static_assert(NMOD <= 8, "mode tables");
   const int period = 2 * m->p + 1;
   std::vector<double> wsum((size_t)period * nz);
   void* sws;
   FE_TRY(fe_ws(m, WS_PCOARSE, sizeof(double) * (nzz + 2 * (size_t)nz) + 64, &sws));
   double* dsum = (double*)sws + nzz + nz;
-  for (int md = 0; md < 4; ++md) {
+  for (int md = 0; md < NMOD; ++md) {
     for (int c = 0; c < period; ++c) {
       k_mode_color<<<fe::grid_for(n), 256, 0, st>>>(mask, plane, NX, tx[md], ty[md], period, c,
                                                     v, n);
@@ -1001,7 +1009,8 @@ static fe_status modes_setup(fe_mesh* m, const unsigned char* mask, double* v, d
         A[(size_t)a * nz + b] = A[(size_t)b * nz + a] = s2;
       }
     if (!spd_inverse(A, nz)) return FE_OK;   // (not expected: planes only)
-    FE_CUDA(cudaMemcpyAsync(dAm + md * nzz, A.data(), sizeof(double) * nzz,
+    std::vector<float> Af(A.begin(), A.end());
+    FE_CUDA(cudaMemcpyAsync(dAm + md * nzz, Af.data(), sizeof(float) * nzz,
                             cudaMemcpyHostToDevice, st));
     FE_CUDA(cudaStreamSynchronize(st));
   }
@@ -1012,7 +1021,7 @@ static fe_status modes_setup(fe_mesh* m, const unsigned char* mask, double* v, d
 
 static fe_status coarse_setup(fe_mesh* m, const fe_poisson_bc* bc, const unsigned char* mask,
                               double* v, double* w, const double** Ainv, const double** cnt,
-                              const double** Amodes, const float** mtab) {
+                              const float** Amodes, const float** mtab) {
   *Ainv = nullptr;
   *cnt = nullptr;
   *Amodes = nullptr;
@@ -1036,9 +1045,9 @@ static fe_status coarse_setup(fe_mesh* m, const fe_poisson_bc* bc, const unsigne
       (!want_modes || m->pc_modes != 0)) {
     if (m->pc_state == 1) { *Ainv = dA; *cnt = dcnt; }
     if (m->pc_state == 1 && want_modes && m->pc_modes == 1) {
-      char* mw = static_cast<char*>(m->ws[WS_PMODES]);
-      *Amodes = reinterpret_cast<const double*>(mw);
-      *mtab = reinterpret_cast<const float*>(mw + sizeof(double) * 4 * (size_t)nz * nz);
+      const float* mw = static_cast<const float*>(m->ws[WS_PMODES]);
+      *Amodes = mw;
+      *mtab = mw + (fe_cg::MODES_NM - 1) * (size_t)nz * nz;
     }
     return FE_OK;
   }
@@ -1187,8 +1196,9 @@ struct CgBuf {
   float* cyf;                  // float coarse correction per plane
   int nseg;                    // segments per plane
   // in-plane mode coarse space (persistent float iteration only; nullptr: planes only):
-  // the four mode inverses [4][nz][nz] and the float mode tables (cos x, sin x, cos y, sin y)
-  const double* Amodes;
+  // the mode inverses [MODES_NM - 1][nz][nz] (float) and the float mode tables (cos x,
+  // sin x, cos y, sin y)
+  const float* Amodes;
   const float* mtab;
 };
 
@@ -1501,7 +1511,7 @@ static fe_status poisson_solve_on(fe_mesh* m, const double* rho, const fe_poisso
   // coarse space of z-planes (z and q serve as scratch before the iteration starts)
   const double* Ainv = nullptr;
   const double* ccnt = nullptr;
-  const double* Amodes = nullptr;
+  const float* Amodes = nullptr;
   const float* mtab = nullptr;
   FE_TRY(coarse_setup(m, bc, mask, z, q, &Ainv, &ccnt, &Amodes, &mtab));
   double* csum = Ainv ? (double*)(ccnt + nzp) : nullptr;
