@@ -101,8 +101,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def traffic_record(kernel_key):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged."""
+def traffic_record(kernel_key, node_vectors):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged, scaled
+    from the record's node-vectors to this launch's (traffic grows with them: the captures
+    keep the tile shape and per-CTA sweep)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[kernel_key]
@@ -116,7 +118,9 @@ def traffic_record(kernel_key):
         return None
     if h != rec.get("source_sha"):
         return None
-    return rec.get("bytes_per_launch")
+    b = rec.get("bytes_per_launch")
+    ref = rec.get("node_vectors")
+    return b * node_vectors / ref if (b and ref) else b
 
 
 class ClockSampler:
@@ -690,7 +694,7 @@ def run_gpu(args):
     kernel_key = {fe.FE_F32: "kron_f32_p5", fe.FE_F64: "kron_f64_p5",
                   fe.FE_F32_F32ACC: "ktc_f32_p5"}.get(prec, "tc_p5")
     # (the nonlocal term adds its own kernels to the filter time: no single-kernel traffic)
-    traffic = traffic_record(kernel_key) if not nl_desc else None
+    traffic = traffic_record(kernel_key, n * nvec) if not nl_desc else None
 
     # end to end through the public API with host buffers.  Every step copies its input block
     # in from pinned host memory (3.1 GB on the benchmark slab) and reads its result back.
