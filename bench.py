@@ -849,9 +849,11 @@ def run_gpu(args):
         conformant = conformant_step(m, slab, X0, a, b, a0, phi, flops_step, dev, fe)
     sweep = None
     variants = {}
+    scf = None
     if rank == 0 and world == 1 and not args.no_extras and args.workload == "p5":
         variants = filter_variants(m, slab, X, phi, a, b, a0, dev, fe)
         sweep = sweep_measure(max(2, min(args.steps, 3)), 2)
+        scf = scf_measure(2, 1)
 
     cpu = None
     if (rank == 0 and world == 1 and not args.no_cpu_baseline
@@ -899,6 +901,8 @@ def run_gpu(args):
             line["conformant"] = conformant
         if sweep is not None:
             variants["sweep"] = sweep
+        if scf is not None:
+            variants["scf"] = scf
         if variants:
             line["variants"] = variants
         print(json.dumps(line))
@@ -930,7 +934,7 @@ def run_sweep(args):
     return 0
 
 
-def run_scf(args):
+def scf_measure(steps, warmup):
     """Self-consistent iterations on the benchmark slab (Hartree level, CEF bias): the time
     of one iteration (Poisson, V_eff, Lanczos bounds, one filter + Rayleigh-Ritz cycle,
     occupations, density, Anderson mixing).  A run of 1 + K iterations and a run of one
@@ -939,7 +943,6 @@ def run_scf(args):
     import torch
     import paper_2504_00998_gb300 as fe
     from paper_2504_00998_gb300 import scf as fscf
-    torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     slab = W.config2()
     m = fe.Mesh.from_slab(slab, device=0)
@@ -959,20 +962,30 @@ def run_scf(args):
         torch.cuda.synchronize(dev)
         return t0.elapsed_time(t1), out
 
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         timed(1)
     t1_ms, _ = timed(1)
-    tk_ms, out = timed(1 + args.steps)
-    ms = (tk_ms - t1_ms) / args.steps
+    tk_ms, out = timed(1 + steps)
+    ms = (tk_ms - t1_ms) / steps
+    m.close()
+    return {"ms_per_iteration": ms, "steps": steps, "warmup": max(warmup, 1),
+            "workload": workload_desc(slab) + "; Hartree-level self-consistent iterations",
+            "run_ms": {"1": t1_ms, str(1 + steps): tk_ms},
+            "mixing_residuals": out["res"], "mu": out["mu"]}
+
+
+def run_scf(args):
+    """The SCF iteration time as its own benchmark line (see scf_measure)."""
+    import torch
+    torch.cuda.set_device(0)
+    r = scf_measure(args.steps, args.warmup)
     print(json.dumps({
-        "metric": "SCF iteration time", "value": ms, "unit": "ms", "n_gpus": 1,
-        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": ms,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": workload_desc(slab) + "; Hartree-level self-consistent iterations",
-                   "parallelism": "single GPU"},
-        "run_ms": {"1": t1_ms, str(1 + args.steps): tk_ms},
-        "mixing_residuals": out["res"], "mu": out["mu"]}))
+        "metric": "SCF iteration time", "value": r["ms_per_iteration"], "unit": "ms",
+        "n_gpus": 1, "steps": r["steps"], "warmup": r["warmup"],
+        "ms_per_step": r["ms_per_iteration"], "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": r["workload"], "parallelism": "single GPU"},
+        "run_ms": r["run_ms"], "mixing_residuals": r["mixing_residuals"], "mu": r["mu"]}))
     return 0
 
 
