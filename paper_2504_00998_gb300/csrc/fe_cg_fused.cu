@@ -17,16 +17,21 @@
 //      p = z + beta p_old itself (the same single rounding its owner uses in step 2);
 //   2. q = sum of the cell copies per node, the owners store the new p, p.q partials;
 //      the block completing the barrier sums the partials and publishes alpha = r.z / p.q;
-//   3. x += alpha p, r -= alpha q on free nodes, sums of r per plane of the block's range;
-//      the completing block forms the coarse right-hand side b_k (plane sums, minus
-//      mean * cnt_k under the CEF projection) and publishes it with the mean;
-//   4. y_j = sum_k Ainv[j][k] b_k for the block's planes, r -= mean (CEF), z = Dinv r + y
-//      on free nodes, r.z and r.r partials; the completing block publishes beta, r.z, r.r,
-//      the iteration count and the convergence test.
+//   3. x += alpha p, r -= alpha q on free nodes, the sums of r against each coarse function
+//      of the planes in the block's range (the plane indicator; with the mode coarse space
+//      also the eight in-plane modes); the completing block forms the coarse right-hand
+//      sides (the indicator's minus mean * cnt_k under the CEF projection) and publishes
+//      them with the mean;
+//   4. the coarse values of the block's planes (a row of the coarse inverse times the
+//      right-hand side, one warp per plane and function), r -= mean (CEF), z = Dinv r plus
+//      the prolongation of the coarse values on free nodes, r.z and r.r partials; the
+//      completing block publishes beta, r.z, r.r, the iteration count and the convergence
+//      test.
 // Every grid sum is taken over the block partials in index order by whichever block
 // completes the barrier (the same code and order whichever it is), so results do not depend
 // on scheduling.  Dot products keep the launch-per-step path's precision: a thread's terms
-// in float, block and grid sums in double.
+// in float, block and grid sums in double (float pairs within a warp).  The mode functions'
+// sums and their coarse solves are in float: they only have to be a fixed linear map.
 //
 // The grid is co-resident by construction (cooperative launch sized from the occupancy
 // calculator).  Every barrier wait is bounded (2 s): a block that gives up sets the state's

@@ -280,19 +280,6 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
   }
 
   auto stored = [&](int gz) { return gz - g.gz_lo >= 0 && gz - g.gz_lo < g.NZs; };
-  // 1/sqrt(mz) and sqrt(mz) of plane gz (1 for the plain stiffness)
-  auto rsq_of = [&](int gz) -> T {
-    if (!cf.mass_scale) return T(1);
-    const int l = gz % P;
-    if (l != 0) return cf.rsq[l];
-    return (gz == 0 || gz == g.nz * P) ? cf.rsq_face : cf.rsq[0];
-  };
-  auto sq_of = [&](int gz) -> T {
-    if (!cf.mass_scale) return T(1);
-    const int l = gz % P;
-    if (l != 0) return cf.sq[l];
-    return (gz == 0 || gz == g.nz * P) ? cf.sq_face : cf.sq[0];
-  };
   auto owned_plane = [&](int gz) {   // planes this segment writes
     return stored(gz) && ((gz >= c0 * P && gz < c1 * P) || (gz == g.nz * P && c1 == g.nz));
   };
@@ -375,7 +362,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
   auto write_plane = [&](int gzo, int j) {
     if (!owned_plane(gzo)) return;
     const int zs = gzo - g.gz_lo;
-    T rs = T(1);
+    T rs = T(1);   // 1 / sqrt(mz) of the plane (local index j; 1 for the plain stiffness)
     if (mass_scale)
       rs = j != 0 ? cf.rsq[j] : ((gzo == 0 || gzo == g.nz * P) ? cf.rsq_face : cf.rsq[0]);
     const T ps = cf.zout * rs;
@@ -627,7 +614,7 @@ __device__ __forceinline__ void kron_body(const KronCoefT<T>& cf, const KronGeom
         w2[i] = W2[item];
       }
       const bool face = gz == 0 || gz == g.nz * P;
-      T sqz = T(1);
+      T sqz = T(1);   // sqrt(mz) of the plane (1 for the plain stiffness)
       if (mass_scale) {
         const int l = k == P ? 0 : k;   // gz % P
         sqz = l != 0 ? cf.sq[l] : (face ? cf.sq_face : cf.sq[0]);
