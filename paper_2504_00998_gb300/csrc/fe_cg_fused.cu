@@ -11,22 +11,24 @@
 // share one contiguous range of nodes (groups of four; the range spans at most MAXSPAN phi
 // planes).
 //
-// One iteration, four barriers:
+// One iteration, three barriers:
 //   1. cell products y_e = K_e p_e of the search direction into the discontinuous grid;
 //      after the first iteration of a launch p is not yet stored: every staged node forms
 //      p = z + beta p_old itself (the same single rounding its owner uses in step 2);
-//   2. q = sum of the cell copies per node, the owners store the new p, p.q partials;
-//      the block completing the barrier sums the partials and publishes alpha = r.z / p.q;
-//   3. x += alpha p, r -= alpha q on free nodes, the sums of r against each coarse function
-//      of the planes in the block's range (the plane indicator; with the mode coarse space
-//      also the eight in-plane modes); the completing block forms the coarse right-hand
-//      sides (the indicator's minus mean * cnt_k under the CEF projection) and publishes
-//      them with the mean;
-//   4. the coarse values of the block's planes (a row of the coarse inverse times the
-//      right-hand side, one warp per plane and function), r -= mean (CEF), z = Dinv r plus
-//      the prolongation of the coarse values on free nodes, r.z and r.r partials; the
-//      completing block publishes beta, r.z, r.r, the iteration count and the convergence
-//      test.
+//   2. q = sum of the cell copies per node, the owners store the new p, p.q partials, and
+//      the sums of q over the free nodes against each coarse function of the planes in the
+//      block's range (the plane indicator; with the mode coarse space also the eight
+//      in-plane modes); the block completing the barrier publishes alpha = r.z / p.q and
+//      the coarse right-hand sides of the new residual r - alpha q, carried by recurrence:
+//      b(r - alpha q) = b(r) - alpha b(q), with b(r) summed exactly from r in a launch's
+//      first iteration (a launch starts after every reliable update, so the recurrence
+//      never runs long); under the CEF projection it also publishes the new residual's
+//      mean and subtracts mean * cnt_k from the indicator's right-hand side;
+//   3. the coarse values of the block's planes (a row of the coarse inverse times the
+//      right-hand side, one warp per plane and function), then in one pass x += alpha p,
+//      r -= alpha q on free nodes, r -= mean (CEF), z = Dinv r plus the prolongation of the
+//      coarse values on free nodes, r.z and r.r partials; the completing block publishes
+//      beta, r.z, r.r, the iteration count and the convergence test.
 // Every grid sum is taken over the block partials in index order by whichever block
 // completes the barrier (the same code and order whichever it is), so results do not depend
 // on scheduling.  Dot products keep the launch-per-step path's precision: a thread's terms
@@ -107,7 +109,10 @@ struct FArgs {
   const double* Ainv;
   const double* cnt;
   double* part;               // [3][G]: p.q, r.z and r.r block partials
-  double* seg;                // [G][MAXSPAN]: sums of r over the planes of each block's nodes
+  double* seg;                // [G][MAXSPAN][NM]: sums of q against the coarse functions of
+                              // the planes of each block's nodes (free nodes)
+  double* seg_r;              // the same for r (a launch's first iteration)
+  double* bprev;              // [NM][nzp]: the coarse right-hand sides of the current r
   double* cbg;                // [nzp]: the coarse right-hand side of the current iteration
   Pub* pub;
   unsigned int* bar;          // [0]: arrivals, [32]: barriers released (0 at launch)
@@ -383,10 +388,70 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
   const float4* d4 = reinterpret_cast<const float4*>(a.dinv);
   const uchar4* m4 = reinterpret_cast<const uchar4*>(a.mask);
 
+  // the block's sums of NM per-thread accumulators to out[(bid * MAXSPAN + sl) * NM + j]:
+  // the indicator's in float pairs (it also carries the mean), the modes' in float
+  auto store_sums = [&](const float (&ms)[NM], double* out, int sl) {
+    const float m0[1] = {ms[0]};
+    block_sum_f<1>(m0, red, redf);
+    if constexpr (NM > 1) {
+      float mm[NM - 1];
+#pragma unroll
+      for (int j = 1; j < NM; ++j) mm[j - 1] = ms[j];
+      block_sum_plain<NM - 1>(mm, yv, redf);
+    }
+    if (tid < NM)
+      out[((int64_t)bid * MAXSPAN + sl) * NM + tid] = tid == 0 ? red[0] : (double)yv[tid - 1];
+  };
+  // the sums of v over the free nodes of the block's range against the coarse functions of
+  // each plane, plane by plane, into out (groups of four nodes; with the mode space a group
+  // lies in one row)
+  auto restrict4 = [&](const float4* v4, double* out) {
+    for (int sl = 0; sl < nsp; ++sl) {
+      const uint32_t pb = (uint32_t)(pl0 + sl) * plane4;
+      const uint32_t lo = max(c0, pb), hi = min(c1, pb + plane4);
+      float ms[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) ms[j] = 0.f;
+      for (uint32_t k = lo + tid; k < hi; k += NT) {
+        float4 v = ldcg4(v4 + k);
+        const uchar4 mv = m4[k];
+        if (mv.x) v.x = 0.f;
+        if (mv.y) v.y = 0.f;
+        if (mv.z) v.z = 0.f;
+        if (mv.w) v.w = 0.f;
+        const float s0 = sum4(v);
+        ms[0] += s0;
+        if constexpr (NM > 1) {
+          const uint32_t i4 = (k - pb) * 4;
+          const uint32_t gy = i4 / (uint32_t)a.NX, gx = i4 - gy * (uint32_t)a.NX;
+          const float4 cx = *reinterpret_cast<const float4*>(mcx + gx);
+          const float4 sx = *reinterpret_cast<const float4*>(msx + gx);
+          const float vc = v.x * cx.x + v.y * cx.y + v.z * cx.z + v.w * cx.w;
+          const float vs = v.x * sx.x + v.y * sx.y + v.z * sx.z + v.w * sx.w;
+          const float cy = mcy[gy], sy = msy[gy];
+          ms[1] += vc;
+          ms[2] += vs;
+          ms[3] += cy * s0;
+          ms[4] += sy * s0;
+          if constexpr (NM == 9) {
+            ms[5] += cy * vc;
+            ms[6] += sy * vc;
+            ms[7] += cy * vs;
+            ms[8] += sy * vs;
+          }
+        }
+      }
+      store_sums(ms, out, sl);
+    }
+  };
+
   bool pending = false;   // p = z + beta p not yet stored
   float bf = 0.f;
   for (int it = 0; it < a.nit; ++it) {
-    // ---- 1. cell products of the search direction (a strip per thread group) ----------
+    // ---- 1. cell products of the search direction (a strip per thread group); in a
+    // launch's first iteration also the exact sums of r against the coarse functions of the
+    // block's planes (later iterations carry them by recurrence)
+    if (it == 0) restrict4(r4, a.seg_r);
     {
       const int g = tid / GT, gt = tid - g * GT;
       float* Ug = reinterpret_cast<float*>(reinterpret_cast<char*>(dsm) + a.grp_off) +
@@ -410,7 +475,8 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
     }
     if (!grid_barrier(a.bar, err, ++nbar, a.pub, &sp, [] {}, false)) return;
 
-    // ---- 2. q = K p (node sums), the stored direction, p.q; alpha -----------------------
+    // ---- 2. q = K p (node sums), the stored direction, p.q, the sums of q over the free
+    // nodes against the coarse functions; alpha and the coarse right-hand sides ----------
     {
       float acc = 0.f;
       const uint32_t n0 = c0 * 4, n1 = c1 * 4;
@@ -445,130 +511,71 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
         }
       }
       const float f[1] = {acc};
-      block_sum_f<1>(f, red, redf);
+      block_sum_f<1>(f, red, redf);   // (its barriers also order the q stores before restrict4)
       if (tid == 0) a.part[bid] = red[0];
+      restrict4(q4, a.seg);
     }
     {
+      // alpha; the coarse right-hand sides of r - alpha q: the sums of r (exact in a launch's
+      // first iteration, else those of the previous iteration, bprev) minus alpha times the
+      // sums of q, each over the blocks whose nodes meet the plane in block order; the CEF
+      // mean of the new residual from the indicator sums, which it then leaves at zero (the
+      // mode functions sum to zero over a plane)
+      const bool first = it == 0;
       auto fin = [&] {
         double t[1];
         sum_parts<1>(a.part, 0, G, t, red);
-        if (tid == 0) {
-          Pub* pb = a.pub;
-          const double alpha = t[0] == 0.0 ? 0.0 : sp.rz / t[0];
-          pb->pq = t[0];
-          pb->alpha = alpha;
-          pb->alphaf = (float)alpha;
-        }
-      };
-      if (!grid_barrier(a.bar, err, ++nbar, a.pub, &sp, fin)) return;
-    }
-
-    // ---- 3. x, r update; per-plane sums of r; the coarse right-hand side ------------------
-    {
-      const float af = sp.alphaf;
-      auto update = [&](uint32_t k) -> float4 {
-        float4 xv = ldcg4(x4 + k), rv = ldcg4(r4 + k);
-        const float4 pv = ldcg4(p4 + k), qv = ldcg4(q4 + k);
-        const uchar4 mv = m4[k];
-        if (!mv.x) { xv.x += af * pv.x; rv.x -= af * qv.x; }
-        if (!mv.y) { xv.y += af * pv.y; rv.y -= af * qv.y; }
-        if (!mv.z) { xv.z += af * pv.z; rv.z -= af * qv.z; }
-        if (!mv.w) { xv.w += af * pv.w; rv.w -= af * qv.w; }
-        x4[k] = xv;
-        r4[k] = rv;
-        return rv;
-      };
-      if constexpr (NM == 1) {
-        float ps[MAXSPAN];
-#pragma unroll
-        for (int j = 0; j < MAXSPAN; ++j) ps[j] = 0.f;
-        for (uint32_t k = c0 + tid; k < c1; k += NT)
-          add_slot<MAXSPAN>(ps, (int)(k / plane4) - pl0, sum4(update(k)));
-        block_sum_f<MAXSPAN>(ps, red, redf);
-        if (tid < MAXSPAN) a.seg[(int64_t)bid * MAXSPAN + tid] = red[tid];
-      } else {
-        // plane by plane: the sums of r against the plane's NM coarse functions (the
-        // indicator, then cos x, sin x, cos y, sin y); a group of four nodes lies in one row
-        for (int sl = 0; sl < nsp; ++sl) {
-          const uint32_t pb = (uint32_t)(pl0 + sl) * plane4;
-          const uint32_t lo = max(c0, pb), hi = min(c1, pb + plane4);
-          float ms[NM];
-#pragma unroll
-          for (int j = 0; j < NM; ++j) ms[j] = 0.f;
-          for (uint32_t k = lo + tid; k < hi; k += NT) {
-            const float4 rv = update(k);
-            const uint32_t i4 = (k - pb) * 4;
-            const uint32_t gy = i4 / (uint32_t)a.NX, gx = i4 - gy * (uint32_t)a.NX;
-            const float4 cx = *reinterpret_cast<const float4*>(mcx + gx);
-            const float4 sx = *reinterpret_cast<const float4*>(msx + gx);
-            const float s0 = sum4(rv);
-            const float rc = rv.x * cx.x + rv.y * cx.y + rv.z * cx.z + rv.w * cx.w;
-            const float rs = rv.x * sx.x + rv.y * sx.y + rv.z * sx.z + rv.w * sx.w;
-            const float cy = mcy[gy], sy = msy[gy];
-            ms[0] += s0;
-            ms[1] += rc;
-            ms[2] += rs;
-            ms[3] += cy * s0;
-            ms[4] += sy * s0;
-            if constexpr (NM == 9) {
-              ms[5] += cy * rc;
-              ms[6] += sy * rc;
-              ms[7] += cy * rs;
-              ms[8] += sy * rs;
-            }
-          }
-          // the indicator's sum in float pairs (it also carries the mean), the modes' in float
-          const float m0[1] = {ms[0]};
-          block_sum_f<1>(m0, red, redf);
-          float mm[NM - 1];
-#pragma unroll
-          for (int j = 1; j < NM; ++j) mm[j - 1] = ms[j];
-          block_sum_plain<NM - 1>(mm, yv, redf);
-          if (tid < NM)
-            a.seg[((int64_t)bid * MAXSPAN + sl) * NM + tid] = tid == 0 ? red[0] : (double)yv[tid - 1];
-        }
-      }
-    }
-    {
-      // the sums of each plane k over the blocks whose nodes meet it (in block order), the
-      // mean under the CEF projection, b_k = sum - mean cnt_k (the mode functions sum to
-      // zero over a plane, so only the indicator's right-hand side carries the mean)
-      auto fin = [&] {
-        // one (coarse function, plane) pair per thread and step
+        const double pq = t[0];
+        const double alpha = pq == 0.0 ? 0.0 : sp.rz / pq;
         for (int e = tid; e < NM * a.nzp; e += NT) {
           const int md = e / a.nzp, k = e - md * a.nzp;
           const uint32_t g0 = (uint32_t)k * plane4, g1 = g0 + plane4 - 1;
           const int b0 = (int)(g0 / a.chunk4), b1 = (int)(g1 / a.chunk4);
-          double sk = 0.0;
+          double sq = 0.0, sr = 0.0;
           for (int b = b0; b <= b1; ++b) {
             const int slot = k - (int)(((uint32_t)b * a.chunk4) / plane4);
-            sk += __ldcg(a.seg + ((int64_t)b * MAXSPAN + slot) * NM + md);
+            const int64_t at = ((int64_t)b * MAXSPAN + slot) * NM + md;
+            sq += __ldcg(a.seg + at);
+            if (first) sr += __ldcg(a.seg_r + at);
           }
-          if (md == 0) cb[k] = sk;
-          else a.cbgf[(md - 1) * a.nzp + k] = (float)sk;
+          const double braw = (first ? sr : __ldcg(a.bprev + e)) - alpha * sq;
+          if (md == 0) {
+            cb[k] = braw;
+          } else {
+            a.bprev[e] = braw;
+            a.cbgf[(md - 1) * a.nzp + k] = (float)braw;
+          }
         }
         __syncthreads();
-        double t[1];
-        sum_parts<1, true>(cb, 0, a.nzp, t, red);
-        const double mn = a.project ? t[0] * a.inv_n : 0.0;
-        for (int k = tid; k < a.nzp; k += NT) a.cbg[k] = cb[k] - mn * a.cnt[k];
+        double tt[1];
+        sum_parts<1, true>(cb, 0, a.nzp, tt, red);
+        const double mn = a.project ? tt[0] * a.inv_n : 0.0;
+        for (int k = tid; k < a.nzp; k += NT) {
+          const double b = cb[k] - mn * a.cnt[k];
+          a.bprev[k] = b;
+          a.cbg[k] = b;
+        }
         if (tid == 0) {
-          a.pub->mean = mn;
-          a.pub->meanf = (float)mn;
+          Pub* pb = a.pub;
+          pb->pq = pq;
+          pb->alpha = alpha;
+          pb->alphaf = (float)alpha;
+          pb->mean = mn;
+          pb->meanf = (float)mn;
         }
       };
       if (!grid_barrier(a.bar, err, ++nbar, a.pub, &sp, fin)) return;
     }
 
-    // ---- 4. coarse correction, preconditioner, r.z and r.r ------------------------------
+    // ---- 3. the coarse values of the block's planes; x += alpha p, r -= alpha q, the CEF
+    // mean, z = Dinv r + the coarse correction; r.z and r.r ---------------------------------
     {
       for (int k = tid; k < a.nzp; k += NT) cb[k] = __ldcg(a.cbg + k);
       float* cbf = reinterpret_cast<float*>(cb + a.nzp);   // (NM > 1) the modes' [NM - 1][nzp]
       for (int k = tid; k < (NM - 1) * a.nzp; k += NT) cbf[k] = __ldcg(a.cbgf + k);
       __syncthreads();
-      // the coarse values of the block's planes, warp w for plane pl0 + w / NM and coarse
-      // function w % NM: y = sum_k Ainv[j][k] b_k (lane l takes k = l, l + 32, ... in order,
-      // then a shuffle tree)
+      // warp w for plane pl0 + w / NM and coarse function w % NM: y = sum_k Ainv[j][k] b_k
+      // (lane l takes k = l, l + 32, ... in order, then a shuffle tree)
       const int lane = tid & 31;
       for (int w = tid >> 5; w < nsp * NM; w += NT / 32) {
         const int sl = w / NM, md = w - sl * NM;
@@ -592,12 +599,22 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
       __syncthreads();
     }
     {
-      const float meanf = sp.meanf;
+      const float af = sp.alphaf, meanf = sp.meanf;
       float a1 = 0.f, a2 = 0.f;
       for (uint32_t k = c0 + tid; k < c1; k += NT) {
-        float4 ri = ldcg4(r4 + k);
+        float4 xv = ldcg4(x4 + k), ri = ldcg4(r4 + k);
+        const float4 pv = ldcg4(p4 + k), qv = ldcg4(q4 + k);
         const float4 dv = d4[k];
         const uchar4 mv = m4[k];
+        if (!mv.x) { xv.x += af * pv.x; ri.x -= af * qv.x; }
+        if (!mv.y) { xv.y += af * pv.y; ri.y -= af * qv.y; }
+        if (!mv.z) { xv.z += af * pv.z; ri.z -= af * qv.z; }
+        if (!mv.w) { xv.w += af * pv.w; ri.w -= af * qv.w; }
+        x4[k] = xv;
+        if (a.project) {
+          ri.x -= meanf; ri.y -= meanf; ri.z -= meanf; ri.w -= meanf;
+        }
+        r4[k] = ri;
         const int sl = (int)(k / plane4) - pl0;
         float4 cv;
         if constexpr (NM == 1) {
@@ -620,10 +637,6 @@ k_cg_fused(const CellCoef cf, const FArgs a) {
           cv.y = base + fc * cx.y + fs * sx.y;
           cv.z = base + fc * cx.z + fs * sx.z;
           cv.w = base + fc * cx.w + fs * sx.w;
-        }
-        if (a.project) {
-          ri.x -= meanf; ri.y -= meanf; ri.z -= meanf; ri.w -= meanf;
-          r4[k] = ri;
         }
         float4 zi;
         zi.x = mv.x ? 0.f : dv.x * ri.x + cv.x;
@@ -782,7 +795,7 @@ fe_status launch(fe_mesh* m, const Plan& pl, const fe_cg::FusedCg& b, int nit,
   // and the barrier words (each on its own 128-byte line); the cell grid is the two-pass
   // operator's scratch
   const size_t nsegs = (size_t)pl.grid * MAXSPAN * NM;
-  const size_t nd = 3 * (size_t)pl.grid + nsegs + (size_t)a.nzp;
+  const size_t nd = 3 * (size_t)pl.grid + 2 * nsegs + (size_t)a.nzp + (size_t)NM * a.nzp;
   const size_t off_cbgf = (sizeof(double) * nd + 127) / 128 * 128;
   const size_t off_pub = (off_cbgf + sizeof(float) * (size_t)(NM - 1) * a.nzp + 127) / 128 * 128;
   const size_t off_bar = off_pub + 256;
@@ -792,7 +805,9 @@ fe_status launch(fe_mesh* m, const Plan& pl, const fe_cg::FusedCg& b, int nit,
   char* wb = static_cast<char*>(w);
   a.part = reinterpret_cast<double*>(wb);
   a.seg = a.part + 3 * (size_t)pl.grid;
-  a.cbg = a.seg + nsegs;
+  a.seg_r = a.seg + nsegs;
+  a.cbg = a.seg_r + nsegs;
+  a.bprev = a.cbg + a.nzp;
   a.cbgf = reinterpret_cast<float*>(wb + off_cbgf);
   a.pub = reinterpret_cast<Pub*>(wb + off_pub);
   a.bar = reinterpret_cast<unsigned int*>(wb + off_bar);
