@@ -46,7 +46,7 @@ def parse():
                          "the tensor cores), f32tc (sum-factorised, split-TF32 in-plane "
                          "contractions on the tensor cores, FP32-accurate)")
     ap.add_argument("--workload", choices=["p5", "p5s", "p3", "sweep", "p5nl", "scf", "p5k",
-                                           "p5q", "p5qs"],
+                                           "p5q", "p5qs", "p5l"],
                     default="p5",
                     help="p5: the benchmark slab; p5s / p3: smaller slabs; sweep: the batched "
                          "bias sweep of 24 independent 8x8xH-cell p=4 slabs; p5nl: the "
@@ -850,10 +850,12 @@ def run_gpu(args):
     sweep = None
     variants = {}
     scf = None
+    large = None
     if rank == 0 and world == 1 and not args.no_extras and args.workload == "p5":
         variants = filter_variants(m, slab, X, phi, a, b, a0, dev, fe)
         sweep = sweep_measure(max(2, min(args.steps, 3)), 2)
         scf = scf_measure(2, 1)
+        large = large_measure(1, 1)
 
     cpu = None
     if (rank == 0 and world == 1 and not args.no_cpu_baseline
@@ -903,6 +905,8 @@ def run_gpu(args):
             variants["sweep"] = sweep
         if scf is not None:
             variants["scf"] = scf
+        if large is not None:
+            variants["large_lcpd"] = large
         if variants:
             line["variants"] = variants
         print(json.dumps(line))
@@ -989,6 +993,121 @@ def run_scf(args):
     return 0
 
 
+def large_measure(steps, warmup):
+    """The large L-CPD slab (48 x 48 x 144 bohr, 24 x 24 x 72 cells, p = 5, 2048 atoms,
+    1024 vectors).  One step = the L-CPD Poisson solve and V_eff, the degree-40 Chebyshev
+    filter of the 1024-wide float array as four 256-vector blocks (each block a column slice,
+    leading dimension 1024), and Rayleigh-Ritz over all 1024 vectors.  Returns the
+    measurements."""
+    import torch
+    import paper_2504_00998_gb300 as fe
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lib = fe.load()
+    slab = W.config5()
+    nvec, degree, nb = slab.nvec, slab.degree, 256
+    m = fe.Mesh.from_slab(slab, device=dev.index)
+    m.set_rr_products(True)
+    phi = torch.empty(m.n_phi, dtype=torch.float64, device=dev)
+    vb = torch.empty(m.n_psi, dtype=torch.float64, device=dev)
+    m.poisson_solve(slab.bias, rtol=POISSON_RTOL, max_iter=40000, phi=phi, vbare=vb)
+    m.set_potential(vb)
+    lo, hi = m.lanczos_bounds(torch.tensor(W.lanczos_start(m.n_psi), device=dev), LANCZOS_STEPS)
+    a = lo + R_FILTER * (hi - lo)
+    X = torch.empty((m.n_psi, nvec), dtype=torch.float32, device=dev)
+    for j in range(nvec // nb):
+        X[:, nb * j:nb * (j + 1)].copy_(
+            torch.from_numpy(W.start_block(slab, nvec=nb, seed=2005 + j)))
+    blocks = [X[:, nb * j:nb * (j + 1)] for j in range(nvec // nb)]
+    st = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    marks, pinfo = [], {}
+
+    def step(rec):
+        e = [ev() for _ in range(4)]
+        e[0].record(st)
+        _, _, info = m.poisson_solve(slab.bias, rtol=POISSON_RTOL, max_iter=40000, phi=phi,
+                                     vbare=vb)
+        pinfo["iters"], pinfo["rel_residual"] = info.iters, info.rel_residual
+        m.set_potential(vb)
+        e[1].record(st)
+        for xb in blocks:
+            m.cheb_filter(xb, degree, a, hi, lo, prec=fe.FE_F32)
+        e[2].record(st)
+        eig = m.rayleigh_ritz(X, prec=fe.FE_F32)
+        e[3].record(st)
+        if rec:
+            marks.append(e)
+        return eig
+
+    for _ in range(warmup):
+        step(False)
+    torch.cuda.synchronize(dev)
+    n0 = lib.fe_kernel_launches()
+    t0, t1 = ev(), ev()
+    with ClockSampler(gpu_index(dev)) as clk:
+        t0.record(st)
+        for _ in range(steps):
+            eig = step(True)
+        t1.record(st)
+        torch.cuda.synchronize(dev)
+    launches = lib.fe_kernel_launches() - n0
+    ms_step = t0.elapsed_time(t1) / steps
+    ph = np.mean([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])]
+                  for e in marks], axis=0)
+    n = m.n_psi
+    flops_hx = nominal_flops_per_hx(slab, nvec)
+    value = flops_hx * (degree + 1) / (ms_step * 1e-3) / 1e12
+    # the dominant kernel: one fused operator launch on one 256-vector block
+    bytes_launch = ((2 + 3 * (degree - 1)) * n * nb * 4 + degree * n * 4) / degree
+    launch_ms = ph[1] / (degree * len(blocks))
+    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    theta = eig.cpu().numpy()
+    out = {
+        "value": value, "unit": "TFLOP/s", "ms_per_step": ms_step, "steps": steps,
+        "warmup": warmup,
+        "workload": (workload_desc(slab) + f"; the 1024-wide float array filtered as "
+                     f"{len(blocks)} blocks of {nb} vectors (leading dimension {nvec}), "
+                     f"Rayleigh-Ritz over all {nvec}"),
+        "l2": "inputs larger than L2 (a %.1f GB array, %.1f GB per block)"
+              % (n * nvec * 4 / 1e9, n * nb * 4 / 1e9),
+        "phases_ms": {"poisson_and_veff": ph[0], "cheb_filter_4_blocks": ph[1],
+                      "cholqr_rr": ph[2]},
+        "poisson": {"iterations": pinfo["iters"], "rel_residual": pinfo["rel_residual"],
+                    "rtol": POISSON_RTOL, "bias": "L-CPD (constrained 12 x 12 bohr patch)"},
+        "filter_tflops": flops_hx * degree / (ph[1] * 1e-3) / 1e12,
+        "ritz_range_ha": [float(theta[0]), float(theta[-1])],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                     "kernel": "kron_f32_p5 (256-vector block, leading dimension 1024)",
+                     "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": launch_ms},
+        "gpu_launches": launches, "clocks": clk.summary()}
+    m.close()
+    del X, blocks
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_large(args):
+    """The large L-CPD slab as its own benchmark line (see large_measure)."""
+    import torch
+    torch.cuda.set_device(0)
+    r = large_measure(args.steps, args.warmup)
+    print(json.dumps({
+        "metric": "Cheb-filter H·X nominal TFLOP/s", "value": r["value"], "unit": "TFLOP/s",
+        "n_gpus": 1, "steps": r["steps"], "warmup": r["warmup"],
+        "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": r["workload"], "parallelism": "single GPU", "l2": r["l2"],
+                   "rr_products": "tc32"},
+        "phases_ms": r["phases_ms"], "poisson": r["poisson"],
+        "filter_tflops": r["filter_tflops"], "ritz_range_ha": r["ritz_range_ha"],
+        "roofline": r["roofline"], "cpu_baseline": None, "e2e": None,
+        "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -997,6 +1116,8 @@ def main():
         return run_sweep(args)
     if args.workload == "scf":
         return run_scf(args)
+    if args.workload == "p5l":
+        return run_large(args)
     return run_gpu(args)
 
 
