@@ -138,6 +138,11 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* a) {
 __device__ __forceinline__ void st_release_u32(unsigned int* a, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* a, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(a), "r"(v) : "memory");
+  return old;
+}
 __device__ __forceinline__ long long global_ns() {
   long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -158,9 +163,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err, unsign
   __shared__ int role;   // 1: completes the barrier, 0: waits, -1: gave up
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned int old = atomicAdd(bar, 1u);
-    __threadfence();
+    // release: the block's writes before the barrier (ordered by the block barrier above);
+    // acquire: the completing block then sees every block's writes
+    const unsigned int old = atom_add_acq_rel_u32(bar, 1u);
     role = old == k * gridDim.x - 1 ? 1 : 0;
   }
   __syncthreads();
@@ -175,7 +180,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err, unsign
     const long long t0 = global_ns();
     unsigned int spins = 0;
     while (ld_acquire_u32(bar + 32) < k) {
-      if (*(volatile int*)err != 0) { role = -1; break; }
+      if ((spins & 15u) == 15u && *(volatile int*)err != 0) { role = -1; break; }
       if (++spins > (1u << 26) || global_ns() - t0 > BAR_TIMEOUT_NS) {
         atomicExch(err, 1);
         role = -1;
@@ -183,7 +188,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err, unsign
       }
       __nanosleep(32);
     }
-    __threadfence();
   }
   __syncthreads();   // the release has been seen (or the wait gave up)
   if (!copy) return role >= 0;
