@@ -702,10 +702,12 @@ def run_gpu(args):
     # (the filtered, rotated block is the iteration's device-resident state, fed to the next
     # step).  The input is the block as it stands after the timed steps (the state a device
     # step starts from, so both loops do the same numerical work); it streams in on a copy
-    # stream while the Poisson solve runs (the solve reads no block), and the filter waits for
-    # it.  A second leg also reads the whole block back every step (two device blocks
-    # alternate; a step's block leaves while the next step's filter runs, the last one after
-    # the last step, inside the timed region) and is reported beside it.
+    # stream into one of two device blocks while the previous step runs (the first step's
+    # under its Poisson solve, which reads no block), and the filter waits for it.  A second
+    # leg also reads the whole block back every step (two device blocks alternate; a step's
+    # block leaves while the next step's filter runs, the last one after the last step, inside
+    # the timed region; its input copy waits for that read-back, so it streams in under the
+    # step's Poisson solve) and is reported beside it.
     Xh = X.cpu().pin_memory()
     eig_h = torch.empty(blk.shape[1], dtype=torch.float64).pin_memory()
     Xbuf = [X, torch.empty_like(X)]
@@ -717,6 +719,7 @@ def run_gpu(args):
         outs = [torch.empty_like(Xh).pin_memory() for _ in range(2)] if read_block else None
         out_done = [None, None]
         pending, marks, d2h = [], [], []
+        nsteps = max(1, min(args.steps, 3))
 
         def read_back(j, fin, eig, after=None):
             cout.wait_event(fin)
@@ -734,17 +737,42 @@ def run_gpu(args):
             out_done[j] = done
             d2h.append((start, done))
 
-        def step(i):
-            j = i % 2 if read_block else 0
-            arrived = ev()
-            cin.wait_stream(st)
-            if out_done[j] is not None:
-                cin.wait_event(out_done[j])
-            e = [ev() for _ in range(5)]
+        # Without the block read-back, step k's input goes to device buffer k % 2 and is
+        # copied in while step k - 1 runs: it waits only for step k - 2, the buffer's last
+        # user (one copy stream, so the copies arrive in step order).
+        h2d = {}
+        fins = {}
+
+        def copy_in(k):
+            jj = k % 2
+            if k >= 2:
+                cin.wait_event(fins[k - 2])
+            start, arr = ev(), ev()
             with torch.cuda.stream(cin):
-                e[0].record(cin)
-                Xbuf[j].copy_(Xh, non_blocking=True)
-                arrived.record(cin)
+                start.record(cin)
+                Xbuf[jj].copy_(Xh, non_blocking=True)
+                arr.record(cin)
+            h2d[k] = (start, arr)
+
+        def step(i):
+            j = i % 2
+            e = [ev() for _ in range(5)]
+            if read_block:
+                arrived = ev()
+                cin.wait_stream(st)
+                if out_done[j] is not None:
+                    cin.wait_event(out_done[j])
+                with torch.cuda.stream(cin):
+                    e[0].record(cin)
+                    Xbuf[j].copy_(Xh, non_blocking=True)
+                    arrived.record(cin)
+            else:
+                if i == 0:
+                    cin.wait_stream(st)
+                    copy_in(0)
+                if i + 1 < nsteps:
+                    copy_in(i + 1)
+                e[0], arrived = h2d[i]
             e[1].record(st)
             m.poisson_solve(slab.bias, rtol=POISSON_RTOL, phi=phi, vbare=vb)
             set_pot()
@@ -759,6 +787,7 @@ def run_gpu(args):
             eig = m.rayleigh_ritz(views[j], prec=prec)
             fin = ev()
             fin.record(st)
+            fins[i] = fin
             if read_block:
                 pending.append((j, fin, eig))
             else:
@@ -768,7 +797,6 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
         t0, t1 = ev(), ev()
         t0.record(st)
-        nsteps = max(1, min(args.steps, 3))
         for i in range(nsteps):
             step(i)
         if pending:
